@@ -1,0 +1,310 @@
+"""Benchmark: one full CSQRP-LSQR solve (count sketch + QR + LSQR) per step on
+the 2D Poisson RFM workload (8 x 8 boxes, J = 200 tanh features each, 30 x 30
+points per box plus boundary and C0/C1 interface rows: m = 65,280, n = 12,800,
+14.4M nonzeros, s = 4n), binary64, synthetic seeded inputs.
+
+Prints one JSON line. `value` is the device time per solve (seconds, lower is
+better) over the whole job; `e2e` is the same solve through the public API with
+host buffers (host->device copy of A and b, device->host copy of x inside the
+timed region). Multi-GPU runs are independent replicas (one instance per rank).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve time to rel. error 1e-10 (sketch+QR+LSQR); SpMV-pair HBM GB/s vs peak"
+WORKLOAD = "2D Poisson RFM, 8x8 boxes, J=200 tanh features, 30x30 points/box, m=65280 n=12800 nnz=14.4M, s=4n"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="csls", choices=["csls", "reference"])
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--config", default="cfg2")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1890.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def qr_flops(s, n):
+    return 2.0 * s * n * n - 2.0 / 3.0 * n ** 3
+
+
+def spmv_pair_bytes(m, n, nnz):
+    # A x and A^T u: values (8 B) + column indices (4 B) per nonzero, row pointers (8 B),
+    # the gathered vector and the written vector, for both passes.
+    return 2 * (12 * nnz) + 8 * (m + 1) + 8 * (n + 1) + 8 * (m + n) * 2
+
+
+# ----------------------------------------------------------------------------- reference arm (CPU oracle)
+
+def oracle_sample_seconds(p, s, iters_full):
+    """Time the oracle on a bounded sample of the workload and scale it to one
+    full solve: the full sketch, Householder QR of the first k columns of the
+    sketch (extrapolated by flop count) and 2 LSQR iterations (scaled by the
+    iteration count the GPU solve needed)."""
+    import oracle
+    t0 = time.perf_counter()
+    h, d = oracle.hash_rows(p.m, s, 1)
+    SA = oracle.sketch(p, s, h, d)
+    t_sketch = time.perf_counter() - t0
+    k = 160
+    sub = np.asfortranarray(SA[:, :k])
+    t0 = time.perf_counter()
+    oracle.householder_qr(sub)
+    t_qr_k = time.perf_counter() - t0
+    flops_k = sum(4.0 * (s - j) * (k - j) for j in range(k))
+    t_qr = t_qr_k * qr_flops(s, p.n) / flops_k
+    R = np.eye(p.n) + np.triu(np.full((p.n, p.n), 1e-3), 1)
+    t0 = time.perf_counter()
+    oracle.lsqr(p, p.b[0], R, "qr", fixed_iters=2)
+    t_it = (time.perf_counter() - t0) / 2.0
+    total = t_sketch + t_qr + t_it * iters_full
+    sample = ("oracle (single-thread C) on %s: full sketch %.2fs + Householder QR of the first %d of %d "
+              "sketch columns %.2fs scaled by flops to %.1fs + 2 LSQR iterations %.2fs/it x %d iterations"
+              % (WORKLOAD, t_sketch, k, p.n, t_qr_k, t_qr, t_it, iters_full))
+    return total, sample, t_sketch + t_qr_k + 2 * t_it
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from workloads import config_problem
+    p = config_problem(args.config)
+    s = 4 * p.n
+    iters = 64
+    vals = []
+    sample = ""
+    for _ in range(args.warmup + args.steps):
+        v, sample, _ = oracle_sample_seconds(p, s, iters)
+        vals.append(v)
+    v = statistics.median(vals[args.warmup:]) if args.steps > 0 else vals[-1]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2409_15818_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+        build.build()
+    from paper_2409_15818_gb300 import csls
+    from workloads import config_problem, poisson2d
+
+    if args.config == "cfg2":
+        p = poisson2d(8, 8, 200, 30, 30, R=2.0, seed=2 + 1000 * rank)   # one instance per replica
+    else:
+        p = config_problem(args.config)
+    m, n, nnz = p.m, p.n, p.nnz
+    s = 4 * n
+    A = csls.Csr.from_numpy(p.row_ptr, p.col, p.val, m, n)
+    b = torch.tensor(p.b[0], device="cuda")
+    opts = dict(seed=1, prec=args.prec, tol=1e-12)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        F = csls.csls_factor(A, **opts)
+        x, rep = csls.csls_solve(F, A, b, raise_on_error=False, **opts)
+        return F, x, rep
+
+    for _ in range(args.warmup):
+        F, x, rep = step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    qr_ms, solve_ms, sketch_ms, iters = [], [], [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        F, x, rep = step()
+        launches += F.report["launches"] + rep["launches"]
+        qr_ms.append(F.report["ms_factor"])
+        sketch_ms.append(F.report["ms_sketch"])
+        solve_ms.append(rep["ms_solve"])
+        iters.append(rep["iterations"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status = rep["status"]
+
+    # SpMV pair (A z, A^T u) timed alone, for the HBM roofline of the Krylov step
+    z = torch.randn(n, dtype=torch.float64, device="cuda")
+    u = torch.randn(m, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        csls.csls_spmv(F, A, z)
+        csls.csls_spmv(F, A, u, trans=True)
+    torch.cuda.synchronize()
+    reps = 50
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(reps):
+        csls.csls_spmv(F, A, z)
+        csls.csls_spmv(F, A, u, trans=True)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    pair_ms = s0.elapsed_time(s1) / reps
+    hbm, bf16, src = peaks()
+    pair_gbs = spmv_pair_bytes(m, n, nnz) / (pair_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    h_row = torch.tensor(p.row_ptr).pin_memory()
+    h_col = torch.tensor(p.col).pin_memory()
+    h_val = torch.tensor(p.val).pin_memory()
+    h_b = torch.tensor(p.b[0]).pin_memory()
+    h_x = torch.empty(n, dtype=torch.float64).pin_memory()
+    h2d = h_row.numel() * 8 + h_col.numel() * 4 + h_val.numel() * 8 + h_b.numel() * 8
+    d2h = n * 8
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 2))
+    q0.record(stream)
+    for _ in range(e2e_steps):
+        A2 = csls.Csr(h_row.cuda(non_blocking=True), h_col.cuda(non_blocking=True), h_val.cuda(non_blocking=True),
+                      m, n)
+        b2 = h_b.cuda(non_blocking=True)
+        F2 = csls.csls_factor(A2, **opts)
+        x2, _ = csls.csls_solve(F2, A2, b2, raise_on_error=False, **opts)
+        h_x.copy_(x2, non_blocking=True)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = q0.elapsed_time(q1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # roofline of the dominant kernel family: the QR (panel + DMMA trailing update)
+    fp64_peak = 2100.0   # GFLOP/s: measured DMMA m16n8k16 .f64 instruction throughput on GB300
+    qr_gflops = qr_flops(s, n) / (statistics.median(qr_ms) * 1e-3) / 1e9
+    cpu = None
+    if rank == 0:
+        total, sample, spent = oracle_sample_seconds(p, s, int(statistics.median(iters)))
+        cpu = {"value": total, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms / 1e3 / world, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec if args.prec == "f64" else "f32 factor / f64 LSQR",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": nnz, "s": s, "tol": 1e-12,
+                       "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (dense sketch 5.2 GB, A 173 MB)"},
+            "status": csls.STATUS_NAMES.get(status, status), "iterations": int(statistics.median(iters)),
+            "phase_ms": {"sketch": statistics.median(sketch_ms), "factor": statistics.median(qr_ms),
+                         "solve": statistics.median(solve_ms)},
+            "roofline": {"bound": "tensor", "kernel": "qr (panel + DMMA f64 trailing update)",
+                         "achieved": qr_gflops / 1e3, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
+                         "frac": qr_gflops / fp64_peak, "traffic": None,
+                         "peak_source": "measured DMMA m16n8k16 f64 instruction rate (2.1 TFLOP/s); "
+                                        "bf16 x nominal fp64/bf16 ratio would give %.2f" % (bf16 * 1.25 / 2250)},
+            "spmv_pair": {"bound": "hbm", "achieved": pair_gbs, "peak": hbm, "unit": "GB/s", "frac": pair_gbs / hbm,
+                          "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * csls.h -- C ABI of the GB300 count-sketch preconditioned LSQR library.
+ *
+ * The library solves the overdetermined sparse least-squares problem
+ *     min_x || A x - b ||_2,   A in R^{m x n}, m >= n,          (Section 1, eq. (1.1))
+ * by the paper's CSQRP-LSQR / CSSVDP-LSQR method (Algorithms 1 and 2): a count
+ * sketch SA with s = gamma n rows (Definition 2.3), a QR (or truncated SVD) of
+ * the s x n sketch giving a right preconditioner, and LSQR on the
+ * preconditioned operator. The preconditioner is applied per step (triangular
+ * solves with R, the form of the Remark after Algorithm 2), so A R^{-1} is never
+ * formed.
+ *
+ * Conventions for every entry point
+ *  - All array pointers are DEVICE pointers unless a comment says "host".
+ *    Arrays are owned by the caller; the library never frees them.
+ *  - Dense matrices are column-major with an explicit leading dimension.
+ *  - Integers are int64_t except CSR column indices (int32_t).
+ *  - The library never calls cudaMalloc/cudaFree. Every call that needs
+ *    scratch memory has a *_workspace query returning the byte counts; the
+ *    caller allocates (any device memory, 256-byte aligned) and passes it in.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream). Calls that return a report synchronise `stream` before returning.
+ *  - Every entry point returns a csls_status (0 = CSLS_OK). No call traps,
+ *    aborts or exits; device-side waits are bounded and report
+ *    CSLS_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef CSLS_H
+#define CSLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* csls_stream_t;
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+    CSLS_OK = 0,
+    CSLS_ERR_ARG = 1,            /* invalid argument, size, layout or CSR structure */
+    CSLS_ERR_RANK_DEFICIENT = 2, /* R has a zero or non-finite diagonal entry (QR variant; cf. Theorem 3.1) */
+    CSLS_ERR_NOT_CONVERGED = 3,  /* LSQR hit maxit before a stopping rule held */
+    CSLS_ERR_BREAKDOWN = 4,      /* alpha or beta became zero with a nonzero residual estimate */
+    CSLS_ERR_NONFINITE = 5,      /* NaN/Inf in A's values, in b or produced during the solve */
+    CSLS_ERR_PRECOND_GUARD = 6,  /* binary32 factor rejected: estimated cond(A R^{-1}) >= opts.guard_cond */
+    CSLS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up (opts.spin_limit) */
+    CSLS_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+    CSLS_ERR_WORKSPACE = 9       /* workspace pointer NULL/misaligned or smaller than the query */
+} csls_status;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* csls_status_string(int status);
+
+/* ---------------------------------------------------------------- types */
+enum { CSLS_VARIANT_QR = 0, CSLS_VARIANT_SVD = 1 };   /* Algorithm 1 / Algorithm 2 */
+enum { CSLS_PREC_F64 = 0, CSLS_PREC_F32 = 1 };        /* arithmetic of the sketch and its factorisation */
+
+/* Sparse A in CSR form. Device pointers, caller-owned. Rows are zero-based;
+ * column indices in [0, n), strictly ascending within each row. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t* row_ptr;   /* m + 1 entries, row_ptr[0] = 0, row_ptr[m] = nnz */
+    const int32_t* col;       /* nnz entries */
+    const double* val;        /* nnz entries */
+} csls_csr;
+
+typedef struct {
+    double gamma;         /* oversampling factor: s = round(gamma n) when s <= 0 (Algorithm 1 step 1) */
+    int64_t s;            /* sketch rows; clamped to m */
+    uint64_t seed;        /* count-sketch hash seed */
+    int variant;          /* CSLS_VARIANT_QR or CSLS_VARIANT_SVD */
+    int factor_prec;      /* CSLS_PREC_F64 or CSLS_PREC_F32 */
+    double rcond;         /* SVD truncation sigma_i > rcond sigma_1; <= 0 means max(s, n) * 2^-53 */
+    double atol, btol;    /* Paige-Saunders stopping tolerances */
+    int64_t maxit;        /* <= 0 means n (Section 4.1) */
+    int64_t fixed_iters;  /* > 0: run exactly this many LSQR iterations, no stopping test */
+    double guard_cond;    /* binary32 factor accepted only if estimated cond(A M) < guard_cond */
+    int64_t spin_limit;   /* iteration bound for every device spin-wait */
+    int64_t check_every;  /* host polls the convergence flag every this many iterations */
+} csls_opts;
+
+/* Defaults: gamma 4, s 0, seed 1, QR, F64, rcond 0, atol = btol = 1e-12,
+ * maxit 0 (= n), fixed_iters 0, guard_cond 10, spin_limit 2e7, check_every 16. */
+void csls_opts_default(csls_opts* opts);
+
+/* Host-side report, filled by csls_factor / csls_solve / csls_solve_backward. */
+typedef struct {
+    int status;
+    int istop;            /* 0 maxit or fixed, 1 rule S1, 2 rule S2, 3 exact (alpha or beta = 0) */
+    int64_t iterations;
+    int64_t s, r;         /* sketch rows used; preconditioner rank (n for QR) */
+    double bnorm;         /* ||b|| */
+    double rnorm;         /* LSQR estimate of ||b - A x|| */
+    double arnorm;        /* LSQR estimate of ||(A M)^T r|| */
+    double anorm;         /* running Frobenius estimate of ||A M|| */
+    double ynorm;         /* ||y|| of the preconditioned problem */
+    double cond_est;      /* cond(A M) from the Golub-Kahan bidiagonal of the last solve (0 if none) */
+    double rdiag_min, rdiag_max;  /* min / max |R_jj| (QR variant) */
+    double ms_sketch, ms_factor, ms_solve;  /* device time per phase (CUDA events) */
+    int64_t launches;     /* kernels launched by the call */
+} csls_report;
+
+typedef struct csls_factor_s csls_factor_t;
+
+/* ---------------------------------------------------------------- sketch */
+/* Count-sketch product SA = Phi D A (Definition 2.3; Algorithm 1 step 2).
+ * Row i of A, times d(i) = +-1, is added to row h(i) of SA, where h(i) and d(i)
+ * come from the SplitMix64 output stream of `seed` (output i = mix(seed + (i+1)
+ * 0x9E3779B97F4A7C15); h = (hi32 * s) >> 32, d = -1 iff the low bit is set).
+ * Each entry of SA is the sum of its contributions in ascending row order,
+ * starting from +0.0, with plain (unfused) additions, so the result is
+ * bit-reproducible. prec = CSLS_PREC_F64 writes double SA; CSLS_PREC_F32 rounds
+ * each value to float first and writes float SA with float sums.
+ *   SA: s x n column-major, leading dimension ld >= s, caller-owned; fully overwritten.
+ * Workspace: csls_sketch_workspace(A, s, &bytes). */
+int csls_sketch_workspace(const csls_csr* A, int64_t s, size_t* bytes);
+int csls_sketch(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, int64_t ld,
+                void* work, size_t work_bytes, csls_stream_t stream);
+
+/* ---------------------------------------------------------------- factor */
+/* Algorithm 1 steps 1-3 (QR variant) or Algorithm 2 steps 1-3 (SVD variant):
+ * sketch, blocked Householder QR of the s x n sketch, R with non-negative
+ * diagonal; for the SVD variant also the one-sided Jacobi SVD R = U Sigma V^T
+ * and P = V_r Sigma_r^{-1} with r = #{sigma_i > rcond sigma_1}. Also builds the
+ * transposed CSR of A used for A^T u.
+ * Two workspaces: `persist` holds the factor (R or P, block inverses, A^T) and
+ * must outlive the handle; `temp` (the dense sketch and QR scratch) may be
+ * released once the call has returned. The handle itself is small host memory
+ * owned by the library: release it with csls_factor_destroy (which frees no
+ * device memory). rep may be NULL. */
+int csls_factor_workspace(const csls_csr* A, const csls_opts* opts, size_t* persist_bytes,
+                          size_t* temp_bytes);
+int csls_factor(const csls_csr* A, const csls_opts* opts, void* persist, size_t persist_bytes,
+                void* temp, size_t temp_bytes, csls_factor_t** factor, csls_report* rep,
+                csls_stream_t stream);
+int csls_factor_destroy(csls_factor_t* factor);
+
+/* Read-only view of a factor for inspection. *R points to the n x n upper
+ * triangle (ld n; double for CSLS_PREC_F64, float for CSLS_PREC_F32) or NULL;
+ * *P to the n x r matrix P (double, ld n) or NULL. Any output may be NULL. */
+int csls_factor_view(const csls_factor_t* factor, int64_t* n, int64_t* s, int64_t* r, int* variant,
+                     int* prec, const void** R, const double** P);
+
+/* ---------------------------------------------------------------- building blocks */
+/* z = M v (trans = 0) or z = M^T v (trans = 1) for the factor's right
+ * preconditioner M = R^{-1} (QR) or M = P (SVD): the per-step application of
+ * Algorithm 1 step 4 in the implicit form. v and z are distinct device vectors
+ * (length n, or r for the y-space side of P). */
+int csls_precond_apply(const csls_factor_t* factor, int trans, const double* v, double* z,
+                       void* work, size_t work_bytes, csls_stream_t stream);
+/* y = A x (trans = 0, x length n, y length m) or y = A^T x (trans = 1), using
+ * the factor's transposed copy of A for the latter. */
+int csls_spmv(const csls_factor_t* factor, const csls_csr* A, int trans, const double* x, double* y,
+              csls_stream_t stream);
+int csls_apply_workspace(const csls_factor_t* factor, size_t* bytes);
+
+/* ---------------------------------------------------------------- solve */
+/* Algorithm 1 steps 4-6 (Algorithm 2 steps 4-6): LSQR (Paige and Saunders 1982)
+ * on min || A M y - b || from y = 0, returning x = M y. nrhs right-hand sides
+ * are solved as independent LSQR recurrences that share each pass over A and
+ * R (block form). b: m x nrhs (ld ldb >= m); x: n x nrhs (ld ldx >= n), both
+ * caller-owned device memory. A must be the matrix the factor was built from.
+ * rep (host, may be NULL) is filled after a stream synchronisation; for nrhs > 1
+ * it reports the first column and the maximum iteration count.
+ * Status: CSLS_ERR_NOT_CONVERGED if maxit was reached before S1/S2 held (x is
+ * still the last iterate); CSLS_ERR_PRECOND_GUARD for a binary32 factor whose
+ * cond estimate is >= guard_cond (x still written). */
+int csls_solve_workspace(const csls_factor_t* factor, int64_t nrhs, size_t* bytes);
+int csls_solve(const csls_factor_t* factor, const csls_csr* A, const double* b, int64_t nrhs,
+               int64_t ldb, double* x, int64_t ldx, const csls_opts* opts, void* work,
+               size_t work_bytes, csls_report* rep, csls_stream_t stream);
+
+/* ---------------------------------------------------------------- backward */
+/* Gradients of a scalar loss L(x) through x = argmin ||A x - b|| (the paper
+ * has no backward pass; implicit differentiation of the normal equations).
+ * With g = dL/dx, lambda = (A^T A)^{-1} g and r = b - A x:
+ *     dL/db = A lambda,    dL/dA_ij = r_i lambda_j - (A lambda)_i x_j  (on A's pattern).
+ * lambda = R^{-1} mu with (B^T B) mu = R^{-T} g, B = A R^{-1}, solved by conjugate
+ * gradients on the well-conditioned B^T B, reusing the forward factor.
+ * grad_b (m) and grad_val (nnz) are device outputs; either may be NULL.
+ * Single right-hand side. */
+int csls_backward_workspace(const csls_factor_t* factor, size_t* bytes);
+int csls_solve_backward(const csls_factor_t* factor, const csls_csr* A, const double* b,
+                        const double* x, const double* grad_x, double* grad_b, double* grad_val,
+                        const csls_opts* opts, void* work, size_t work_bytes, csls_report* rep,
+                        csls_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSLS_H */

@@ -1,0 +1,155 @@
+// Device-side LSQR state and the fused step helpers shared by the triangular
+// solve, SpMV and dense-preconditioner kernels.
+//
+// Vector conventions (single right-hand side), following Paige and Saunders:
+//   ut  = beta_{i} u_i       (u kept unnormalised; 1/beta folded into A^T u)
+//   vt  = alpha_i v_i        (v kept unnormalised; 1/alpha folded into M v)
+//   z   = M v_i              (M = R^{-1} or P)
+//   wx  = M w_i              (search direction mapped to x-space)
+//   x   = M y_i              (tracked directly)
+#pragma once
+
+#include "csls_internal.cuh"
+
+namespace csls {
+
+struct TrsvCtl {
+    unsigned epoch;    // completed launches; flags of the current launch are set to epoch + 1
+    unsigned ticket;   // block-row tickets handed out by the current launch
+    unsigned done;     // CTAs finished in the current launch
+    unsigned pad;
+};
+
+struct LsqrState {
+    // recurrence (Paige-Saunders names)
+    double alpha, beta;        // alpha_i and beta_{i+1} (beta_i before the SpMV of iteration i)
+    double rhobar, phibar;
+    double cx, cw;             // x += cx wx ; wx = z - cw wx   (applied in the next M-apply)
+    double anorm2, bnorm, rnorm, arnorm, ynorm;
+    double cs2, sn2, zz, xxnorm;   // ||y|| estimate (Paige-Saunders xnorm recurrence)
+    double inv_beta;
+    double atol, btol;
+    long long iter, maxit, fixed, hist_cap;
+    int done, istop, first, err;
+    unsigned spmv_cnt, apply_cnt;
+    TrsvCtl up, lo;
+};
+
+// Last-CTA detection: every CTA calls this after publishing its partial.
+__device__ __forceinline__ bool last_cta(unsigned* counter, unsigned nblocks) {
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(counter, 1u);
+        is_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+// Fixed-order sum of nb partials (called by one thread).
+__device__ __forceinline__ double sum_partials(const double* p, int nb) {
+    double t = 0.0;
+    for (int i = 0; i < nb; ++i) t += __ldcg(p + i);
+    return t;
+}
+
+// Epilogue of M v_i for element k of the x-space vectors.
+__device__ __forceinline__ void xw_update(LsqrState* st, int first, double cx, double cw, double zk, double* wx,
+                                          double* x, int64_t k) {
+    if (first) {
+        wx[k] = zk;
+    } else {
+        const double w = wx[k];
+        x[k] += cx * w;
+        wx[k] = zk - cw * w;
+    }
+}
+
+// One scalar step of LSQR after alpha_{i+1} is known (run by a single thread).
+__device__ __forceinline__ void lsqr_scalar_step(LsqrState* st, double alpha_new, double* hist) {
+    const double beta = st->beta;
+    const double alpha_old = st->alpha;
+    st->anorm2 += alpha_old * alpha_old + beta * beta;
+    const double rhobar = st->rhobar, phibar = st->phibar;
+    const double rho = sqrt(rhobar * rhobar + beta * beta);
+    const double c = rhobar / rho, sn = beta / rho;
+    const double theta = sn * alpha_new;
+    const double phi = c * phibar;
+    st->rhobar = -c * alpha_new;
+    st->phibar = sn * phibar;
+    // ||y|| estimate
+    const double delta = st->sn2 * rho, gambar = -st->cs2 * rho;
+    const double rhs = phi - delta * st->zz;
+    const double zbar = rhs / gambar;
+    st->ynorm = sqrt(st->xxnorm + zbar * zbar);
+    const double gamma = sqrt(gambar * gambar + theta * theta);
+    st->cs2 = gambar / gamma;
+    st->sn2 = theta / gamma;
+    st->zz = rhs / gamma;
+    st->xxnorm += st->zz * st->zz;
+    st->cx = phi / rho;
+    st->cw = theta / rho;
+    st->alpha = alpha_new;
+    st->rnorm = st->phibar;
+    st->arnorm = st->phibar * alpha_new * fabs(c);
+    st->iter += 1;
+    if (hist && st->iter <= st->hist_cap) {
+        hist[2 * st->iter] = alpha_new;
+        hist[2 * st->iter + 1] = beta;
+    }
+    const double anorm = sqrt(st->anorm2);
+    int stop = 0, istop = 0;
+    if (!isfinite(rho) || !isfinite(alpha_new) || !isfinite(st->phibar)) {
+        stop = 1;
+        set_error(&st->err, CSLS_ERR_NONFINITE);
+    } else if (alpha_new == 0.0 || beta == 0.0) {
+        stop = 1; istop = 3;
+    } else if (st->fixed > 0) {
+        stop = st->iter >= st->fixed;
+    } else {
+        if (st->rnorm <= st->btol * st->bnorm + st->atol * anorm * st->ynorm) { stop = 1; istop = 1; }
+        else if (st->arnorm <= st->atol * anorm * st->rnorm) { stop = 1; istop = 2; }
+        else if (st->iter >= st->maxit) { stop = 1; istop = 0; }
+    }
+    st->istop = istop;
+    if (stop) st->done = 1;
+}
+
+// ------------------------------------------------------------------ launchers (solve building blocks)
+
+struct TrsvArgs {
+    const void* R;          // n x n upper (ld n), double or float
+    int rprec;              // CSLS_PREC_*
+    const double* Dinv;
+    int64_t n;
+    int nb;                 // ceil(n / 64)
+};
+
+// mode 0: z = R^{-1} v. mode 1: LSQR step (v scaled by 1/alpha, x / wx epilogue).
+int launch_trsv_upper(const TrsvArgs& a, int mode, const double* v, double* z, int* flags, TrsvCtl* ctl,
+                      LsqrState* st, double* wx, double* x, long long spin, int* err, cudaStream_t s);
+// mode 0: z = R^{-T} g (in place allowed: z == g). mode 1: LSQR step vt = R^{-T} g - (beta/alpha) vt,
+// alpha update and scalar step. mode 2: LSQR start vt = R^{-T} g, alpha_1.
+int launch_trsv_lower(const TrsvArgs& a, int mode, double* g, double* vt, double* out, int* flags, TrsvCtl* ctl,
+                      LsqrState* st, double* partials, double* hist, long long spin, int* err, cudaStream_t s);
+
+// mode 0: y = A x. mode 1: ut = A z - (alpha/beta) ut, beta update. mode 2: ut = b copy, beta_1.
+int launch_spmv(const csls_csr* A, int mode, const double* x, double* y, LsqrState* st, double* partials,
+                int grid, cudaStream_t s);
+// y = A^T x * scale (scale = 1 for mode 0, st->inv_beta for mode 1).
+int launch_spmv_t(const Transpose& AT, int64_t n, int64_t m, int64_t nnz, int mode, const double* x, double* y,
+                  LsqrState* st, cudaStream_t s);
+int spmv_grid(const csls_csr* A);
+
+// Dense preconditioner P (n x r, ld n) for the SVD variant.
+// mode 0: z = P v. mode 1: LSQR step z = P (vt / alpha) with x / wx epilogue.
+int launch_pgemv(const double* P, int64_t n, int64_t r, int mode, const double* v, double* z, LsqrState* st,
+                 double* wx, double* x, cudaStream_t s);
+// mode 0: y = P^T g. mode 1: vt = P^T g - (beta/alpha) vt + alpha update + scalar step. mode 2: start.
+int launch_pgemv_t(const double* P, int64_t n, int64_t r, int mode, const double* g, double* vt, double* out,
+                   LsqrState* st, double* partials, double* hist, cudaStream_t s);
+
+}  // namespace csls

@@ -1,0 +1,163 @@
+// One-sided Jacobi SVD of R (Hestenes; Demmel and Veselic 1992) for the
+// CSSVDP preconditioner (Algorithm 2 step 3): SA = Q R, so SA and R share Sigma
+// and V. Column pairs of G = R are orthogonalised by plane rotations in the
+// round-robin (circle) order: each step rotates n/2 disjoint pairs, one CTA per
+// pair, accumulating the same rotations into V. Sweeps repeat until no pair
+// needs a rotation. Then P = V_r Sigma_r^{-1} keeps sigma_i > rcond sigma_1.
+#include <algorithm>
+#include <vector>
+
+#include "csls_internal.cuh"
+
+namespace csls {
+
+constexpr int kJacThreads = 256;
+
+__global__ void __launch_bounds__(kJacThreads)
+k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double tol, unsigned* rotations) {
+    __shared__ double red[3][kJacThreads / 32];
+    __shared__ double cs_s[2];
+    __shared__ int skip_s;
+    const int64_t pidx = blockIdx.x;   // pair index in [0, N/2)
+    int64_t a, b;
+    if (pidx == 0) {
+        a = step % (N - 1);
+        b = N - 1;
+    } else {
+        a = (step + pidx) % (N - 1);
+        b = (step - pidx + (N - 1)) % (N - 1);
+    }
+    if (a > b) { int64_t t = a; a = b; b = t; }
+    if (b >= n) return;   // padding column
+    double* ga = G + a * n;
+    double* gb = G + b * n;
+    double saa = 0.0, sbb = 0.0, sab = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kJacThreads) {
+        const double x = ga[i], y = gb[i];
+        saa += x * x; sbb += y * y; sab += x * y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        saa += __shfl_xor_sync(0xffffffffu, saa, o);
+        sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
+        sab += __shfl_xor_sync(0xffffffffu, sab, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = saa; red[1][threadIdx.x >> 5] = sbb; red[2][threadIdx.x >> 5] = sab;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0, C = 0.0;
+        for (int w = 0; w < kJacThreads / 32; ++w) { A += red[0][w]; B += red[1][w]; C += red[2][w]; }
+        if (C == 0.0 || fabs(C) <= tol * sqrt(A * B)) {
+            skip_s = 1;
+        } else {
+            skip_s = 0;
+            const double zeta = (B - A) / (2.0 * C);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            cs_s[0] = c;
+            cs_s[1] = c * t;
+            atomicAdd(rotations, 1u);
+        }
+    }
+    __syncthreads();
+    if (skip_s) return;
+    const double c = cs_s[0], s = cs_s[1];
+    double* va = V + a * n;
+    double* vb = V + b * n;
+    for (int64_t i = threadIdx.x; i < n; i += kJacThreads) {
+        const double x = ga[i], y = gb[i];
+        ga[i] = c * x - s * y;
+        gb[i] = s * x + c * y;
+        const double p = va[i], q = vb[i];
+        va[i] = c * p - s * q;
+        vb[i] = s * p + c * q;
+    }
+}
+
+__global__ void k_copy_init(const double* R, double* G, double* V, int64_t n) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        G[idx] = R[idx];
+        V[idx] = (idx % n == idx / n) ? 1.0 : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kJacThreads) k_col_norms(const double* G, int64_t n, double* sigma) {
+    __shared__ double red[kJacThreads / 32];
+    const double* g = G + (int64_t)blockIdx.x * n;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kJacThreads) s += g[i] * g[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kJacThreads / 32; ++w) t += red[w];
+        sigma[blockIdx.x] = sqrt(t);
+    }
+}
+
+__global__ void k_form_p(const double* V, const double* sigma, const int* order, int64_t n, int64_t r, double* P,
+                         double* sigma_sorted) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * r;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx % n, k = idx / n;
+        const int src = order[k];
+        P[i + k * n] = V[i + (int64_t)src * n] / sigma[src];
+        if (i == 0) sigma_sorted[k] = sigma[src];
+    }
+}
+
+int svd_precond(const double* R, int64_t n, double rcond, double* G, double* V, double* sigma, double* P, int* order,
+                int64_t* r_out, int* err, cudaStream_t st, int64_t* launches) {
+    (void)err;
+    const int64_t N = n + (n & 1);
+    k_copy_init<<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 65535), 256, 0, st>>>(R, G, V, n);
+    CSLS_CUDA(cudaGetLastError());
+    // rotations counter lives in the first word of `order` until the ordering is written
+    unsigned* rot = reinterpret_cast<unsigned*>(order);
+    const double tol = 1e-15;
+    int64_t nl = 1;
+    for (int sweep = 0; sweep < 60 && N >= 2; ++sweep) {
+        CSLS_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned), st));
+        for (int64_t step = 0; step < N - 1; ++step) {
+            k_jacobi_step<<<(unsigned)(N / 2), kJacThreads, 0, st>>>(G, V, n, N, step, tol, rot);
+            CSLS_CUDA(cudaGetLastError());
+        }
+        nl += N - 1;
+        unsigned h_rot = 0;
+        CSLS_CUDA(cudaMemcpyAsync(&h_rot, rot, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CSLS_CUDA(cudaStreamSynchronize(st));
+        if (h_rot == 0) break;
+    }
+    // sigma_j = ||G_j||, sorted descending on the host (n values)
+    double* sig_raw = P;   // scratch: P is rewritten below
+    k_col_norms<<<(unsigned)n, kJacThreads, 0, st>>>(G, n, sig_raw);
+    CSLS_CUDA(cudaGetLastError());
+    std::vector<double> hs((size_t)n);
+    CSLS_CUDA(cudaMemcpyAsync(hs.data(), sig_raw, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CSLS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> ord((size_t)n);
+    for (int64_t i = 0; i < n; ++i) ord[(size_t)i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return hs[(size_t)x] > hs[(size_t)y]; });
+    int64_t r = 0;
+    const double s1 = n > 0 ? hs[(size_t)ord[0]] : 0.0;
+    while (r < n && hs[(size_t)ord[(size_t)r]] > rcond * s1) ++r;
+    // sigma (device) <- raw norms, order (device) <- permutation; P <- V_r Sigma_r^{-1}
+    CSLS_CUDA(cudaMemcpyAsync(sigma, hs.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st));
+    CSLS_CUDA(cudaMemcpyAsync(order, ord.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+    CSLS_CUDA(cudaStreamSynchronize(st));
+    if (r > 0) {
+        k_form_p<<<(unsigned)std::min<int64_t>(ceil_div(n * r, 256), 65535), 256, 0, st>>>(V, sigma, order, n, r, P,
+                                                                                             G);
+        CSLS_CUDA(cudaGetLastError());
+        // sorted singular values end up in G[0..r) ; copy them to sigma
+        CSLS_CUDA(cudaMemcpyAsync(sigma, G, sizeof(double) * (size_t)r, cudaMemcpyDeviceToDevice, st));
+    }
+    *r_out = r;
+    if (launches) *launches += nl + 2;
+    return CSLS_OK;
+}
+
+}  // namespace csls

@@ -1,0 +1,260 @@
+// Blocked triangular solves with R (the per-step preconditioner of the implicit
+// form, Remark after Algorithm 2), one kernel per solve.
+//
+// R is cut into 64 x 64 blocks. One CTA owns one block row (upper solve) or
+// block column (transposed solve); CTAs take block indices from an atomic
+// ticket in launch order, so a CTA only ever waits for blocks owned by CTAs that
+// started before it and the chain always progresses. Finished blocks are
+// published with a release store of the launch epoch into a per-block flag;
+// consumers acquire it with a bounded spin. The diagonal blocks are applied
+// through their precomputed inverses, so both the solve with R and the one with
+// R^T apply the same fixed operator and its exact transpose.
+#include "lsqr.cuh"
+
+namespace csls {
+
+constexpr int kTs = kTrsvBlock;   // 64
+constexpr int kTsThreads = 256;   // 4 threads per row / column
+
+__device__ __forceinline__ bool wait_flag(const int* flag, int want, long long spin, int* err) {
+    long long it = 0;
+    while (ld_acquire(flag) != want) {
+        if (++it > spin) {
+            set_error(err, CSLS_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+template <class TR>
+__device__ __forceinline__ double ldr(const TR* p) { return (double)__ldg(p); }
+
+// z = R^{-1} v  (MODE 0)   |   z = R^{-1} (vt / alpha) with the x / wx epilogue (MODE 1)
+template <class TR, int MODE>
+__global__ void __launch_bounds__(kTsThreads)
+k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restrict__ Dinv, const double* v,
+             double* z, int* flags, TrsvCtl* ctl, LsqrState* st, double* wx, double* x, long long spin, int* err) {
+    __shared__ int sb_s;
+    __shared__ unsigned epoch_s;
+    __shared__ double part[4][kTs];
+    __shared__ double rhs[kTs];
+    __shared__ double coef[4];
+    const int tid = threadIdx.x;
+    if (MODE == 1 && *(volatile int*)&st->done) return;
+    if (tid == 0) {
+        epoch_s = *(volatile unsigned*)&ctl->epoch;
+        sb_s = (int)atomicAdd(&ctl->ticket, 1u);
+        if (MODE == 1) {
+            coef[0] = 1.0 / st->alpha;
+            coef[1] = st->cx;
+            coef[2] = st->cw;
+            coef[3] = (double)st->first;
+        } else {
+            coef[0] = 1.0;
+        }
+    }
+    __syncthreads();
+    const int want = (int)(epoch_s + 1u);
+    const int b = nb - 1 - sb_s;
+    const int64_t r0 = (int64_t)b * kTs;
+    const int bs = (int)(n - r0 < kTs ? n - r0 : kTs);
+    const int row = tid & (kTs - 1), q = tid >> 6;
+    double acc = 0.0;
+    for (int c = nb - 1; c > b; --c) {
+        const int64_t c0 = (int64_t)c * kTs;
+        const int cs = (int)(n - c0 < kTs ? n - c0 : kTs);
+        if (tid == 0) wait_flag(&flags[c], want, spin, err);
+        __syncthreads();
+        if (row < bs) {
+            const TR* rp = R + (r0 + row) + (c0 + q * 16) * n;
+            const double* zp = z + c0 + q * 16;
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk)
+                if (q * 16 + kk < cs) acc += ldr(rp + (int64_t)kk * n) * __ldcg(zp + kk);
+        }
+    }
+    part[q][row] = acc;
+    __syncthreads();
+    if (tid < kTs) {
+        double r = 0.0;
+        if (tid < bs) r = v[r0 + tid] * coef[0] - (((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid]);
+        rhs[tid] = r;
+    }
+    __syncthreads();
+    const double* D = Dinv + (int64_t)b * kTs * kTs;
+    double a2 = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const int k = q * 16 + kk;
+        a2 += D[row + k * kTs] * rhs[k];
+    }
+    part[q][row] = a2;
+    __syncthreads();
+    if (tid < bs) {
+        const double zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
+        z[r0 + tid] = zb;
+        if (MODE == 1) xw_update(st, coef[3] != 0.0, coef[1], coef[2], zb, wx, x, r0 + tid);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        st_release(&flags[b], want);
+        unsigned prev = atomicAdd(&ctl->done, 1u);
+        if (prev == (unsigned)nb - 1) {
+            ctl->ticket = 0;
+            ctl->done = 0;
+            if (MODE == 1) st->first = 0;
+            __threadfence();
+            atomicAdd(&ctl->epoch, 1u);
+        }
+    }
+}
+
+// MODE 0: out = R^{-T} g.  MODE 1: vt = R^{-T} g - (beta/alpha) vt, then alpha and the scalar step.
+// MODE 2: vt = R^{-T} g, alpha_1 and the LSQR start values.
+// The solve runs in place in g (block b's entries of g are read only by block b before
+// being replaced by the solution, which later blocks then read).
+template <class TR, int MODE>
+__global__ void __launch_bounds__(kTsThreads)
+k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restrict__ Dinv, double* g, double* vt,
+             double* out, int* flags, TrsvCtl* ctl, LsqrState* st, double* partials, double* hist, long long spin,
+             int* err) {
+    __shared__ int sb_s;
+    __shared__ unsigned epoch_s;
+    __shared__ double part[4][kTs];
+    __shared__ double rhs[kTs];
+    __shared__ double coef[2];
+    __shared__ double red[kTsThreads / 32];
+    const int tid = threadIdx.x;
+    if (MODE == 1 && *(volatile int*)&st->done) return;
+    if (tid == 0) {
+        epoch_s = *(volatile unsigned*)&ctl->epoch;
+        sb_s = (int)atomicAdd(&ctl->ticket, 1u);
+        coef[0] = MODE == 1 ? st->beta / st->alpha : 0.0;
+    }
+    __syncthreads();
+    const int want = (int)(epoch_s + 1u);
+    const int b = sb_s;
+    const int64_t r0 = (int64_t)b * kTs;
+    const int bs = (int)(n - r0 < kTs ? n - r0 : kTs);
+    const int col = tid & (kTs - 1), q = tid >> 6;
+    double acc = 0.0;
+    for (int c = 0; c < b; ++c) {
+        const int64_t c0 = (int64_t)c * kTs;
+        if (tid == 0) wait_flag(&flags[c], want, spin, err);
+        __syncthreads();
+        if (col < bs) {
+            const TR* rp = R + (c0 + q * 16) + (r0 + col) * n;   // column r0+col, rows c0+q*16..+16
+            const double* zp = g + c0 + q * 16;
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) acc += ldr(rp + kk) * __ldcg(zp + kk);
+        }
+    }
+    part[q][col] = acc;
+    __syncthreads();
+    if (tid < kTs) {
+        double r = 0.0;
+        if (tid < bs) r = g[r0 + tid] - (((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid]);
+        rhs[tid] = r;
+    }
+    __syncthreads();
+    const double* D = Dinv + (int64_t)b * kTs * kTs;
+    double a2 = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const int k = q * 16 + kk;
+        a2 += D[k + col * kTs] * rhs[k];   // (D^T rhs)_col
+    }
+    part[q][col] = a2;
+    __syncthreads();
+    double sq = 0.0;
+    if (tid < bs) {
+        const double zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
+        g[r0 + tid] = zb;
+        if (MODE == 0) {
+            if (out != g) out[r0 + tid] = zb;
+        } else {
+            const double vn = MODE == 1 ? zb - coef[0] * vt[r0 + tid] : zb;
+            vt[r0 + tid] = vn;
+            sq = vn * vn;
+        }
+    }
+    if (MODE != 0) {
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if ((tid & 31) == 0) red[tid >> 5] = sq;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        if (MODE != 0) {
+            double t = 0.0;
+            for (int w = 0; w < kTsThreads / 32; ++w) t += red[w];
+            partials[b] = t;
+            __threadfence();
+        }
+        st_release(&flags[b], want);
+        unsigned prev = atomicAdd(&ctl->done, 1u);
+        if (prev == (unsigned)nb - 1) {
+            __threadfence();
+            if (MODE != 0) {
+                const double alpha_new = sqrt(sum_partials(partials, nb));
+                if (MODE == 1) {
+                    lsqr_scalar_step(st, alpha_new, hist);
+                } else {
+                    st->alpha = alpha_new;
+                    st->rhobar = alpha_new;
+                    if (hist) hist[0] = alpha_new;
+                    if (alpha_new == 0.0 || !isfinite(alpha_new)) {
+                        st->done = 1;
+                        st->istop = 3;
+                        if (!isfinite(alpha_new)) set_error(&st->err, CSLS_ERR_NONFINITE);
+                    }
+                }
+            }
+            ctl->ticket = 0;
+            ctl->done = 0;
+            __threadfence();
+            atomicAdd(&ctl->epoch, 1u);
+        }
+    }
+}
+
+int launch_trsv_upper(const TrsvArgs& a, int mode, const double* v, double* z, int* flags, TrsvCtl* ctl,
+                      LsqrState* st, double* wx, double* x, long long spin, int* err, cudaStream_t s) {
+    dim3 grid((unsigned)a.nb), block(kTsThreads);
+    if (a.rprec == CSLS_PREC_F64) {
+        const double* R = (const double*)a.R;
+        if (mode == 0) k_trsv_upper<double, 0><<<grid, block, 0, s>>>(R, a.n, a.nb, a.Dinv, v, z, flags, ctl, st, wx, x, spin, err);
+        else k_trsv_upper<double, 1><<<grid, block, 0, s>>>(R, a.n, a.nb, a.Dinv, v, z, flags, ctl, st, wx, x, spin, err);
+    } else {
+        const float* R = (const float*)a.R;
+        if (mode == 0) k_trsv_upper<float, 0><<<grid, block, 0, s>>>(R, a.n, a.nb, a.Dinv, v, z, flags, ctl, st, wx, x, spin, err);
+        else k_trsv_upper<float, 1><<<grid, block, 0, s>>>(R, a.n, a.nb, a.Dinv, v, z, flags, ctl, st, wx, x, spin, err);
+    }
+    CSLS_CUDA(cudaGetLastError());
+    return CSLS_OK;
+}
+
+int launch_trsv_lower(const TrsvArgs& a, int mode, double* g, double* vt, double* out, int* flags, TrsvCtl* ctl,
+                      LsqrState* st, double* partials, double* hist, long long spin, int* err, cudaStream_t s) {
+    dim3 grid((unsigned)a.nb), block(kTsThreads);
+#define CSLS_LOWER(TR, MD)                                                                                      \
+    k_trsv_lower<TR, MD><<<grid, block, 0, s>>>((const TR*)a.R, a.n, a.nb, a.Dinv, g, vt, out, flags, ctl, st, \
+                                                 partials, hist, spin, err)
+    if (a.rprec == CSLS_PREC_F64) {
+        if (mode == 0) CSLS_LOWER(double, 0);
+        else if (mode == 1) CSLS_LOWER(double, 1);
+        else CSLS_LOWER(double, 2);
+    } else {
+        if (mode == 0) CSLS_LOWER(float, 0);
+        else if (mode == 1) CSLS_LOWER(float, 1);
+        else CSLS_LOWER(float, 2);
+    }
+#undef CSLS_LOWER
+    CSLS_CUDA(cudaGetLastError());
+    return CSLS_OK;
+}
+
+}  // namespace csls

@@ -1,0 +1,313 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs, at sizes the oracle finishes in seconds that still span
+several tiles, panels and a ragged tail.
+
+Tolerances:
+  * sketch: bit-exact (binary64 and binary32), same hash and ascending-row order;
+  * R: relative difference <= 1e-12 on well-conditioned sketches; on the
+    ill-conditioned RFM sketches the backward error ||R^T R - SA^T SA|| / ||SA||^2
+    is checked instead (the R factor itself is then only determined to about
+    cond(SA) * 2^-53);
+  * solution: with cond(A) moderate, ||x - x_oracle|| / ||x_oracle|| <= 1e-10;
+    on RFM matrices (cond(A) ~ 1e9) x is only determined up to cond(A) * 2^-53,
+    so the A-norm ||A (x - x_oracle)|| / ||A x_oracle|| (the norm Theorem 3.3
+    bounds) must be <= max(1e-10, 2 x the spread between the two independent
+    oracle solvers), and the residual norms must agree to 1e-12 ||b||.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests.helpers import CSR, csr_from_dense, random_sparse
+from workloads import config_problem, poisson2d, scaled_random_sparse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def csls():
+    from paper_2409_15818_gb300 import build
+    build.build()
+    from paper_2409_15818_gb300 import csls as mod
+    return mod
+
+
+def dev(csls, p):
+    return csls.Csr.from_numpy(p.row_ptr, p.col, p.val, p.m, p.n)
+
+
+def gpu_sketch(csls, A, s, seed, prec):
+    t = csls.csls_sketch(A, s, seed, prec=prec)
+    torch.cuda.synchronize()
+    return t.cpu().numpy().T[:s, :]
+
+
+SKETCH_CASES = {
+    "cfg1": lambda: config_problem("cfg1"),
+    "ragged_rfm": lambda: poisson2d(3, 2, 37, 11, 9, R=1.5, seed=7),
+    "cfg5_slice": lambda: config_problem("cfg5_slice"),
+}
+
+
+@pytest.mark.parametrize("case", list(SKETCH_CASES))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_sketch_bit_exact(csls, case, prec):
+    p = SKETCH_CASES[case]()
+    for s, seed in ((4 * p.n if 4 * p.n < p.m else p.m, 11), (p.m // 3 + 1, 12345)):
+        got = gpu_sketch(csls, dev(csls, p), s, seed, prec)
+        h, d = oracle.hash_rows(p.m, s, seed)
+        want = oracle.sketch(p, s, h, d, np.float64 if prec == "f64" else np.float32)
+        assert got.shape == want.shape
+        assert np.array_equal(got.view(np.uint64 if prec == "f64" else np.uint32),
+                              np.asarray(want).view(np.uint64 if prec == "f64" else np.uint32))
+
+
+@pytest.mark.parametrize("s", [1, 2, 97])
+def test_sketch_degenerate_bucket_counts(csls, s):
+    """Very few buckets: every bucket holds many rows (long-segment sort paths)."""
+    p = scaled_random_sparse(9000, 30, per_row=3, cond_exp=1.0, seed=3)
+    got = gpu_sketch(csls, dev(csls, p), s, 5, "f64")
+    h, d = oracle.hash_rows(p.m, s, 5)
+    want = oracle.sketch(p, s, h, d)
+    assert np.array_equal(got, want)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_factor_r_matches_oracle_well_conditioned(csls):
+    rng = np.random.default_rng(21)
+    A = random_sparse(3000, 200, 12, rng)   # 200 = 6 panels of 32 + 8, 4 TRSV blocks (ragged)
+    F = csls.csls_factor(dev(csls, A), s=800, seed=9)
+    R = F.R().cpu().numpy()
+    fac = oracle.factor(A, 800, 9)
+    assert _rel(R, fac["R"]) < 1e-12
+    assert np.all(np.diag(R) >= 0) and np.all(np.tril(R, -1) == 0)
+    F32 = csls.csls_factor(dev(csls, A), s=800, seed=9, prec="f32")
+    R32 = F32.R().cpu().numpy().astype(np.float64)
+    R32o = oracle.r_factor(oracle.sketch(A, 800, *oracle.hash_rows(A.m, 800, 9), np.float32))
+    assert _rel(R32, R32o) < 1e-5 and _rel(R32, fac["R"]) < 1e-5
+
+
+def test_factor_backward_error_rfm(csls):
+    p = config_problem("cfg1")
+    F = csls.csls_factor(dev(csls, p), seed=11)
+    R = F.R().cpu().numpy()
+    h, d = oracle.hash_rows(p.m, 4 * p.n, 11)
+    SA = oracle.sketch(p, 4 * p.n, h, d)
+    err = np.linalg.norm(R.T @ R - SA.T @ SA) / np.linalg.norm(SA) ** 2
+    assert err < 50 * p.n * 2.0 ** -53
+    Ro = oracle.factor(p, 4 * p.n, 11)["R"]
+    assert _rel(R, Ro) < 1e-6
+    assert F.report["rdiag_min"] > 0 and F.report["s"] == 4 * p.n
+
+
+def test_precond_apply_and_spmv_pair(csls):
+    rng = np.random.default_rng(22)
+    A = random_sparse(2500, 150, 9, rng, scale_exp=3.0)
+    Ad = dev(csls, A)
+    F = csls.csls_factor(Ad, s=600, seed=4)
+    R = F.R().cpu().numpy()
+    v = rng.standard_normal(150)
+    vt = torch.tensor(v, device="cuda")
+    z = csls.csls_precond_apply(F, vt).cpu().numpy()
+    zt = csls.csls_precond_apply(F, vt, trans=True).cpu().numpy()
+    assert _rel(z, oracle.trsv_upper(R, v)) < 1e-12
+    assert _rel(zt, oracle.trsv_upper_trans(R, v)) < 1e-12
+    x = rng.standard_normal(150)
+    u = rng.standard_normal(2500)
+    y = csls.csls_spmv(F, Ad, torch.tensor(x, device="cuda")).cpu().numpy()
+    g = csls.csls_spmv(F, Ad, torch.tensor(u, device="cuda"), trans=True).cpu().numpy()
+    assert _rel(y, oracle.spmv(A, x)) < 1e-14
+    assert _rel(g, oracle.spmv_trans(A, u)) < 1e-14
+
+
+def test_solve_well_conditioned_x_space(csls):
+    """cond(A) ~ 1e3: the solution is determined to ~1e-13, so x itself must match."""
+    rng = np.random.default_rng(23)
+    A = random_sparse(4000, 230, 10, rng, scale_exp=3.0)
+    b = rng.standard_normal(4000)
+    F = csls.csls_factor(dev(csls, A), s=920, seed=6)
+    x, rep = csls.csls_solve(F, dev(csls, A), torch.tensor(b, device="cuda"), tol=1e-14, maxit=400)
+    _, xo, info = oracle.csqrp_lsqr(A, b, s=920, seed=6, tol=1e-14, maxit=400)
+    assert _rel(x.cpu().numpy(), xo) < 1e-10
+    assert rep["istop"] in (1, 2) and abs(rep["iterations"] - info["iterations"]) <= 3
+    assert rep["cond_est"] < 10
+
+
+def _anorm_rel(Ad, x, xo):
+    return np.linalg.norm(Ad @ (x - xo)) / np.linalg.norm(Ad @ xo)
+
+
+@pytest.mark.parametrize("case", ["cfg1", "ragged_rfm"])
+def test_solve_rfm_matches_oracle(csls, case):
+    p = SKETCH_CASES[case]()
+    Ad = p.dense()
+    b = p.b[0]
+    F = csls.csls_factor(dev(csls, p), seed=11)
+    x, rep = csls.csls_solve(F, dev(csls, p), torch.tensor(b, device="cuda"))
+    x = x.cpu().numpy()
+    fac, xo, info = oracle.csqrp_lsqr(p, b, seed=11)
+    x_hh, _ = oracle.hhqr_solve(Ad, b)
+    spread = _anorm_rel(Ad, x_hh, xo)
+    assert _anorm_rel(Ad, x, xo) <= max(1e-10, 2 * spread)
+    r_gpu = np.linalg.norm(b - Ad @ x)
+    r_orc = np.linalg.norm(b - Ad @ xo)
+    assert abs(r_gpu - r_orc) <= 1e-12 * np.linalg.norm(b)
+    assert abs(rep["rnorm"] - r_gpu) <= 1e-9 * np.linalg.norm(b)
+    assert rep["istop"] in (1, 2) and rep["cond_est"] < 10
+
+
+def test_fixed_iterations_track_oracle(csls):
+    """Early iterates match the oracle's when both preconditioners agree to
+    rounding (a well-conditioned sketch; on the RFM sketches the two R factors
+    differ by ~cond(SA) 2^-53, which already moves the early iterates)."""
+    rng = np.random.default_rng(26)
+    A = random_sparse(3000, 150, 10, rng, scale_exp=3.0)
+    b = rng.standard_normal(3000)
+    F = csls.csls_factor(dev(csls, A), s=600, seed=5)
+    fac = oracle.factor(A, 600, 5)
+    for k in (1, 2, 4, 8):
+        x, rep = csls.csls_solve(F, dev(csls, A), torch.tensor(b, device="cuda"), fixed_iters=k)
+        xo, info = oracle.lsqr(A, b, fac["R"], "qr", fixed_iters=k)
+        assert rep["iterations"] == k
+        assert _rel(x.cpu().numpy(), xo) < 1e-10
+
+
+def test_multi_rhs_equals_single(csls):
+    p = poisson2d(3, 2, 37, 11, 9, R=1.5, seed=7, modes=((1, 1), (2, 1), (1, 3)))
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=3)
+    B = torch.tensor(p.b, device="cuda")
+    X, rep = csls.csls_solve(F, A, B)
+    for k in range(3):
+        xk, _ = csls.csls_solve(F, A, B[k])
+        assert torch.equal(X[k], xk)
+
+
+def test_svd_variant_rank_deficient(csls):
+    rng = np.random.default_rng(24)
+    base = random_sparse(900, 40, 6, rng).dense()
+    Ad = np.concatenate([base, base[:, :5] @ rng.standard_normal((5, 6))], axis=1)   # rank 40 of 46
+    b = rng.standard_normal(900)
+    A = csr_from_dense(Ad)
+    F = csls.csls_factor(dev(csls, A), s=184, seed=2, variant="svd")
+    x, rep = csls.csls_solve(F, dev(csls, A), torch.tensor(b, device="cuda"), variant="svd", tol=1e-14, maxit=200)
+    assert rep["r"] == 40
+    x_mn = np.linalg.lstsq(Ad, b, rcond=None)[0]
+    assert _rel(x.cpu().numpy(), x_mn) < 1e-9
+    fac, xo, _ = oracle.csqrp_lsqr(A, b, s=184, seed=2, variant="svd", tol=1e-14, maxit=200)
+    assert fac["r"] == 40 and _rel(x.cpu().numpy(), xo) < 1e-9
+
+
+def test_svd_variant_full_rank_cfg1(csls):
+    p = config_problem("cfg1")
+    b = p.b[0]
+    F = csls.csls_factor(dev(csls, p), seed=11, variant="svd")
+    x, rep = csls.csls_solve(F, dev(csls, p), torch.tensor(b, device="cuda"), variant="svd")
+    fac, xo, _ = oracle.csqrp_lsqr(p, b, seed=11, variant="svd")
+    Ad = p.dense()
+    x_hh, _ = oracle.hhqr_solve(Ad, b)
+    assert rep["r"] == fac["r"]
+    assert _anorm_rel(Ad, x.cpu().numpy(), xo) <= max(1e-10, 2 * _anorm_rel(Ad, x_hh, xo))
+
+
+def test_backward_matches_oracle_adjoint(csls):
+    prob = scaled_random_sparse(1000, 100, per_row=10, cond_exp=4.0, seed=5)
+    A = CSR(prob.m, prob.n, prob.row_ptr, prob.col, prob.val)
+    b = prob.b[0]
+    Ag = dev(csls, prob)
+    F = csls.csls_factor(Ag, seed=8)
+    bt = torch.tensor(b, device="cuda")
+    x, _ = csls.csls_solve(F, Ag, bt, tol=1e-14, maxit=300)
+    gx = 2.0 * (x - torch.tensor(prob.x_true, device="cuda"))
+    gb, gv, rep = csls.csls_solve_backward(F, Ag, bt, x, gx, tol=1e-14, maxit=300)
+    x_hh, RA = oracle.hhqr_solve(A.dense(), b)
+    lam, gbo, gvo = oracle.adjoint(A, b, x.cpu().numpy(), RA, gx.cpu().numpy())
+    assert _rel(gb.cpu().numpy(), gbo) < 1e-9
+    assert _rel(gv.cpu().numpy(), gvo) < 1e-9
+
+
+def test_autograd_function(csls):
+    prob = scaled_random_sparse(600, 40, per_row=6, cond_exp=2.0, seed=9)
+    A = dev(csls, prob)
+    val = A.val.clone().requires_grad_(True)
+    b = torch.tensor(prob.b[0], device="cuda", requires_grad=True)
+    x = csls.CslsSolve.apply(val, b, A.row_ptr, A.col, A.m, A.n, dict(tol=1e-14, maxit=200))
+    loss = ((x - torch.tensor(prob.x_true, device="cuda")) ** 2).sum()
+    loss.backward()
+    Ad = CSR(prob.m, prob.n, prob.row_ptr, prob.col, prob.val)
+    x_hh, RA = oracle.hhqr_solve(Ad.dense(), prob.b[0])
+    _, gbo, gvo = oracle.adjoint(Ad, prob.b[0], x.detach().cpu().numpy(), RA,
+                                 2.0 * (x.detach().cpu().numpy() - prob.x_true))
+    assert _rel(b.grad.cpu().numpy(), gbo) < 1e-9
+    assert _rel(val.grad.cpu().numpy(), gvo) < 1e-9
+
+
+# ----------------------------------------------------------------------------- status codes
+
+def test_nonfinite_rhs(csls):
+    p = config_problem("cfg1")
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=1)
+    b = torch.tensor(p.b[0], device="cuda")
+    b[17] = float("nan")
+    x, rep = csls.csls_solve(F, A, b, raise_on_error=False)
+    assert rep["status"] == 5
+
+
+def test_nonfinite_matrix(csls):
+    p = config_problem("cfg1")
+    val = p.val.copy()
+    val[123] = np.inf
+    A = csls.Csr.from_numpy(p.row_ptr, p.col, val, p.m, p.n)
+    with pytest.raises(csls.CslsError) as e:
+        csls.csls_factor(A, seed=1)
+    assert e.value.status == 5
+
+
+def test_rank_deficient_qr(csls):
+    rng = np.random.default_rng(25)
+    Ad = random_sparse(500, 20, 5, rng).dense()
+    Ad[:, 7] = 0.0   # a zero column: R(7, 7) = 0
+    with pytest.raises(csls.CslsError) as e:
+        csls.csls_factor(dev(csls, csr_from_dense(Ad)), s=80, seed=1)
+    assert e.value.status == 2
+
+
+def test_not_converged(csls):
+    p = config_problem("cfg1")
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=1)
+    x, rep = csls.csls_solve(F, A, torch.tensor(p.b[0], device="cuda"), maxit=2, raise_on_error=False)
+    assert rep["status"] == 3 and rep["iterations"] == 2
+
+
+def test_bounded_wait_timeout_then_recovery(csls):
+    """spin_limit 0 makes every grid-barrier wait give up at once: the factor
+    returns CSLS_ERR_TIMEOUT instead of hanging, and the context stays usable."""
+    p = config_problem("cfg1")
+    A = dev(csls, p)
+    with pytest.raises(csls.CslsError) as e:
+        csls.csls_factor(A, seed=1, spin_limit=0)
+    assert e.value.status == 7
+    F = csls.csls_factor(A, seed=1)
+    x, rep = csls.csls_solve(F, A, torch.tensor(p.b[0], device="cuda"))
+    assert rep["status"] == 0
+
+
+def test_f32_factor_guard(csls):
+    p = config_problem("cfg1")
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=11, prec="f32")
+    x, rep = csls.csls_solve(F, A, torch.tensor(p.b[0], device="cuda"), prec="f32", raise_on_error=False)
+    assert rep["status"] in (0, 6)
+    assert (rep["status"] == 6) == (rep["cond_est"] >= 10)
+    Ad = p.dense()
+    _, xo, _ = oracle.csqrp_lsqr(p, p.b[0], seed=11)
+    x_hh, _ = oracle.hhqr_solve(Ad, p.b[0])
+    assert _anorm_rel(Ad, x.cpu().numpy(), xo) <= max(1e-9, 4 * _anorm_rel(Ad, x_hh, xo))
+    rep2 = csls.csls_solve(F, A, torch.tensor(p.b[0], device="cuda"), guard_cond=1.0001, raise_on_error=False)[1]
+    assert rep2["status"] == 6
