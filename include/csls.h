@@ -119,6 +119,26 @@ int csls_sketch_workspace(const csls_csr* A, int64_t s, size_t* bytes);
 int csls_sketch(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, int64_t ld,
                 void* work, size_t work_bytes, csls_stream_t stream);
 
+/* Same result as csls_sketch, for callers that cannot call cudaMalloc
+ * themselves -- for example code whose device memory is entirely owned by
+ * another framework's pool allocator, or latency-critical paths where the
+ * implicit device synchronisation of cudaMalloc is not acceptable. (The paper
+ * has no counterpart; this is a library convenience.)
+ * Instead of a caller workspace it uses a fixed 16 MiB scratch array that the
+ * library keeps in device memory: every GPU that loads the library holds those
+ * 16 MiB until the process exits. The call allocates nothing. Sizes whose
+ * scratch needs exceed 16 MiB (roughly 4 m + 16 s bytes) are rejected with
+ * CSLS_ERR_WORKSPACE before any device work; use csls_sketch for those.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call before
+ * any stream capture. All calls share the one array and each call starts by
+ * clearing what must start at zero, so calls that overlap on the GPU (different
+ * streams, or different host threads on the same device) race and must be
+ * serialised by the caller. Arguments, layout and results are those of
+ * csls_sketch. */
+int csls_sketch_noalloc(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, int64_t ld,
+                        csls_stream_t stream);
+
 /* ---------------------------------------------------------------- factor */
 /* Algorithm 1 steps 1-3 (QR variant) or Algorithm 2 steps 1-3 (SVD variant):
  * sketch, blocked Householder QR of the s x n sketch, R with non-negative

@@ -60,6 +60,8 @@ EXPORTS = {
     "csls_sketch_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "csls_sketch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "csls_sketch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "csls_factor_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "csls_factor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
@@ -184,6 +186,20 @@ def csls_sketch(A, s, seed, prec="f64", SA=None, ld=None, stream=None):
     _check(_lib().csls_sketch(ctypes.byref(a), s, seed, PREC[prec], _ptr(SA), ld, _ptr(work), work.numel(),
                               _stream(stream)), "csls_sketch")
     return SA
+
+
+def csls_sketch_noalloc(A, s, seed, prec="f64", SA=None, ld=None, stream=None, raise_on_error=True):
+    """csls_sketch on the library's fixed scratch area (no workspace allocation);
+    returns (SA, status)."""
+    ld = int(ld or s)
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    if SA is None:
+        SA = torch.empty((A.n, ld), dtype=dtype, device=A.val.device)
+    a = A.struct()
+    st = _lib().csls_sketch_noalloc(ctypes.byref(a), s, seed, PREC[prec], _ptr(SA), ld, _stream(stream))
+    if raise_on_error:
+        _check(st, "csls_sketch_noalloc")
+    return SA, st
 
 
 class Factor:

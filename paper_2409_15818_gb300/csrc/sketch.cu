@@ -143,3 +143,54 @@ int sketch_run(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, 
 }
 
 }  // namespace csls
+
+// ======================================================================= no-allocation variant
+//
+// csls_sketch_noalloc runs csls_sketch with a fixed, library-owned scratch area
+// instead of a caller workspace. The area is a file-scope __device__ array, so
+// every GPU that loads the library holds these bytes until the process exits.
+// Host code cannot use the array's name as a device address; its address is
+// looked up once per device with cudaGetSymbolAddress (with that device current)
+// on the first call made on that device.
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // 16 MiB
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_sketch_scratch[kNoAllocScratchBytes];
+
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CSLS_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return CSLS_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sketch_scratch) != cudaSuccess || !p) return CSLS_ERR_CUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return CSLS_OK;
+}
+
+}  // namespace
+
+extern "C" int csls_sketch_noalloc(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, int64_t ld,
+                                   csls_stream_t stream) {
+    if (!A || s <= 0 || s > 2147483647LL) return CSLS_ERR_ARG;
+    size_t need = 0;
+    const int rc = csls_sketch_workspace(A, s, &need);
+    if (rc != CSLS_OK) return rc;
+    if (need > kNoAllocScratchBytes) return CSLS_ERR_WORKSPACE;   // beyond the static maximum
+    void* scratch = nullptr;
+    const int sc = noalloc_scratch(&scratch);
+    if (sc != CSLS_OK) return sc;
+    // csls_sketch clears every scratch entry that must start at zero.
+    return csls_sketch(A, s, seed, prec, SA, ld, scratch, kNoAllocScratchBytes, stream);
+}
