@@ -90,6 +90,8 @@ def config_problem(name):
     cfg4a      cfg2's matrix with 64 right-hand sides sin(a pi x) sin(b pi y), a, b in 1..8
     cfg5       2,000,000 x 20,000, 10 per row, columns scaled over 10 decades, seed 5
     cfg5_slice 1,000 x 100 with the cfg5 recipe
+    rfm6x6     2D Poisson, 6x6 boxes, J=200, 30x30 points, R=2, seed 2     36,720 x 7,200 (profiling size:
+               its 28,800 x 7,200 sketch is 1.7 GB, above L2 and well below HBM)
     """
     if name == "cfg1":
         return poisson2d(2, 2, 100, 20, 20, R=1.0, seed=1)
@@ -102,6 +104,8 @@ def config_problem(name):
         return poisson2d(8, 8, 200, 30, 30, R=2.0, seed=2, modes=modes)
     if name == "cfg5":
         return scaled_random_sparse(2_000_000, 20_000, seed=5)
+    if name == "rfm6x6":
+        return poisson2d(6, 6, 200, 30, 30, R=2.0, seed=2)
     if name == "cfg5_slice":
         return scaled_random_sparse(1000, 100, seed=5)
     raise KeyError(name)
