@@ -31,7 +31,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="csls", choices=["csls", "reference"])
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--prec", default="f64emu", choices=["f64", "f32", "f64emu"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 solve timed beside")
     ap.add_argument("--config", default="cfg2")
     return ap.parse_args()
 
@@ -224,6 +225,25 @@ def main():
         ms = float(t.item())
     status = rep["status"]
 
+    # the plain binary64 form (trailing updates on the FP64 MMA pipe), timed once beside the chosen form
+    plain = None
+    if args.prec != "f64" and not args.no_compare:
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        popts = dict(opts, prec="f64")
+        p0.record(stream)
+        Fp = csls.csls_factor(A, **popts)
+        xp, repp = csls.csls_solve(Fp, A, b, raise_on_error=False, **popts)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        Ap = torch.sparse_csr_tensor(A.row_ptr, A.col.to(torch.int64), A.val, (m, n))
+        dx = xp - x
+        rel_a = float(torch.linalg.vector_norm(torch.mv(Ap, dx)) / torch.linalg.vector_norm(torch.mv(Ap, xp)))
+        plain = {"dtype": "f64", "s_per_solve": p0.elapsed_time(p1) / 1e3, "iterations": int(repp["iterations"]),
+                 "status": csls.STATUS_NAMES.get(repp["status"], repp["status"]),
+                 "factor_ms": Fp.report["ms_factor"], "solve_ms": repp["ms_solve"],
+                 "rel_diff_A_norm_vs_chosen": rel_a}
+        del Fp, xp
+
     # SpMV pair (A z, A^T u) timed alone, for the HBM roofline of the Krylov step
     z = torch.randn(n, dtype=torch.float64, device="cuda")
     u = torch.randn(m, dtype=torch.float64, device="cuda")
@@ -283,7 +303,9 @@ def main():
         line = {
             "metric": METRIC, "value": ms / 1e3 / world, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.prec if args.prec == "f64" else "f32 factor / f64 LSQR",
+            "vs_baseline": None,
+            "dtype": {"f64": "f64", "f32": "f32 factor / f64 LSQR",
+                      "f64emu": "f64 (trailing-update products from exact bf16 digit products)"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": nnz, "s": s, "tol": 1e-12,
                        "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
@@ -291,8 +313,10 @@ def main():
             "status": csls.STATUS_NAMES.get(status, status), "iterations": int(statistics.median(iters)),
             "phase_ms": {"sketch": statistics.median(sketch_ms), "factor": statistics.median(qr_ms),
                          "solve": statistics.median(solve_ms)},
-            "roofline": {"bound": "tensor", "kernel": "qr (panel + DMMA f64 trailing update)",
-                         "achieved": qr_gflops / 1e3, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
+            "roofline": {"bound": "tensor", "kernel": "qr (panel + trailing update, %s)" % (
+                             "DMMA f64" if args.prec == "f64" else
+                             "exact bf16 digit products on mma.sync" if args.prec == "f64emu" else "FP32 FMA"),
+                         "achieved": qr_gflops / 1e3, "peak": fp64_peak / 1e3, "unit": "TFLOP/s (FP64-equivalent)",
                          "frac": qr_gflops / fp64_peak, "traffic": None,
                          "peak_source": "measured DMMA m16n8k16 f64 rate with full-mantissa operands (1.10 TFLOP/s, "
                                         "= cuBLAS DGEMM); bf16 x nominal fp64/bf16 ratio would give %.2f"
@@ -300,6 +324,7 @@ def main():
             "spmv_pair": {"bound": "hbm", "achieved": pair_gbs, "peak": hbm, "unit": "GB/s", "frac": pair_gbs / hbm,
                           "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src},
             "cpu_baseline": cpu,
+            "plain_f64_beside": plain,
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,

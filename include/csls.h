@@ -55,7 +55,15 @@ const char* csls_status_string(int status);
 
 /* ---------------------------------------------------------------- types */
 enum { CSLS_VARIANT_QR = 0, CSLS_VARIANT_SVD = 1 };   /* Algorithm 1 / Algorithm 2 */
-enum { CSLS_PREC_F64 = 0, CSLS_PREC_F32 = 1 };        /* arithmetic of the sketch and its factorisation */
+/* Arithmetic of the sketch and its factorisation:
+ *   CSLS_PREC_F64      binary64 throughout (trailing updates on the FP64 MMA pipe);
+ *   CSLS_PREC_F32      binary32 sketch and QR (accepted only under the cond guard);
+ *   CSLS_PREC_F64_EMU  binary64 sketch and panels; the trailing-update products are computed
+ *                      exactly from 8-bit digit pieces on the bf16 tensor cores and the trailing
+ *                      matrix is kept in 62-bit fixed point per column: each product carries a
+ *                      relative error of about 2^-38 of (sum |v| |c|), far below what the
+ *                      preconditioner needs; R is stored in binary64. */
+enum { CSLS_PREC_F64 = 0, CSLS_PREC_F32 = 1, CSLS_PREC_F64_EMU = 2 };
 
 /* Sparse A in CSR form. Device pointers, caller-owned. Rows are zero-based;
  * column indices in [0, n), strictly ascending within each row. */
@@ -71,7 +79,7 @@ typedef struct {
     int64_t s;            /* sketch rows; clamped to m */
     uint64_t seed;        /* count-sketch hash seed */
     int variant;          /* CSLS_VARIANT_QR or CSLS_VARIANT_SVD */
-    int factor_prec;      /* CSLS_PREC_F64 or CSLS_PREC_F32 */
+    int factor_prec;      /* CSLS_PREC_F64, CSLS_PREC_F32 or CSLS_PREC_F64_EMU */
     double rcond;         /* SVD truncation sigma_i > rcond sigma_1; <= 0 means max(s, n) * 2^-53 */
     double atol, btol;    /* Paige-Saunders stopping tolerances */
     int64_t maxit;        /* <= 0 means n (Section 4.1) */

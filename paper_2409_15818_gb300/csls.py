@@ -20,7 +20,7 @@ STATUS_NAMES = {
     8: "CSLS_ERR_CUDA", 9: "CSLS_ERR_WORKSPACE",
 }
 VARIANT = {"qr": 0, "svd": 1}
-PREC = {"f64": 0, "f32": 1}
+PREC = {"f64": 0, "f32": 1, "f64emu": 2}
 
 
 class CslsError(RuntimeError):
@@ -176,7 +176,7 @@ def csls_status_string(status):
 def csls_sketch(A, s, seed, prec="f64", SA=None, ld=None, stream=None):
     """SA = S A (s x n column-major); returns the tensor viewed as (n, ld) row-major storage."""
     ld = int(ld or s)
-    dtype = torch.float64 if prec == "f64" else torch.float32
+    dtype = torch.float32 if prec == "f32" else torch.float64
     if SA is None:
         SA = torch.empty((A.n, ld), dtype=dtype, device=A.val.device)
     a = A.struct()

@@ -77,7 +77,7 @@ struct FactorPersist {
 static FactorPersist persist_carve(Carve& c, const csls_csr* A, const csls_opts* o) {
     FactorPersist f;
     const int64_t n = A->n;
-    const int esz = o->factor_prec == CSLS_PREC_F32 ? 4 : 8;
+    const int esz = o->factor_prec == CSLS_PREC_F32 ? 4 : 8;   // R storage
     f.R = c.take<char>((size_t)(n * n * esz));
     f.Dinv = c.take<double>((size_t)(ceil_div(n, kTrsvBlock) * kTrsvBlock * kTrsvBlock));
     f.AT.row_ptr = c.take<int64_t>((size_t)n + 1);
@@ -106,6 +106,8 @@ struct FactorTemp {
     double* G;
     double* V;
     int* order;
+    void* emu;
+    size_t emu_bytes;
 };
 
 static FactorTemp temp_carve(Carve& c, const csls_csr* A, const csls_opts* o, int64_t s) {
@@ -127,6 +129,12 @@ static FactorTemp temp_carve(Carve& c, const csls_csr* A, const csls_opts* o, in
     } else {
         t.G = t.V = nullptr;
         t.order = nullptr;
+    }
+    t.emu = nullptr;
+    t.emu_bytes = 0;
+    if (o->factor_prec == CSLS_PREC_F64_EMU) {
+        t.emu_bytes = qr_emu_scratch_bytes(s, n);
+        t.emu = c.take<char>(t.emu_bytes);
     }
     return t;
 }
@@ -415,8 +423,9 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
     CSLS_TRY(check_csr(A));
     if (!o || !factor) return CSLS_ERR_ARG;
     if (o->variant != CSLS_VARIANT_QR && o->variant != CSLS_VARIANT_SVD) return CSLS_ERR_ARG;
-    if (o->factor_prec != CSLS_PREC_F64 && o->factor_prec != CSLS_PREC_F32) return CSLS_ERR_ARG;
-    if (o->variant == CSLS_VARIANT_SVD && o->factor_prec != CSLS_PREC_F64) return CSLS_ERR_ARG;
+    if (o->factor_prec != CSLS_PREC_F64 && o->factor_prec != CSLS_PREC_F32 && o->factor_prec != CSLS_PREC_F64_EMU)
+        return CSLS_ERR_ARG;
+    if (o->variant == CSLS_VARIANT_SVD && o->factor_prec == CSLS_PREC_F32) return CSLS_ERR_ARG;
     size_t pb = 0, tb = 0;
     CSLS_TRY(csls_factor_workspace(A, o, &pb, &tb));
     if (!persist || !temp || persist_bytes < pb || temp_bytes < tb || !aligned256(persist) || !aligned256(temp))
@@ -439,12 +448,17 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
     CSLS_TRY(transpose_build(A, fp.AT, ft.tcounts, ft.tcursor, ft.err, st, &launches));
     // sketch + QR
     EventTimer t_sk(st);
-    CSLS_TRY(sketch_run(A, s, o->seed, o->factor_prec, ft.SA, ft.ld, ft.sk, ft.err, st, &launches));
+    const int sk_prec = o->factor_prec == CSLS_PREC_F32 ? CSLS_PREC_F32 : CSLS_PREC_F64;
+    CSLS_TRY(sketch_run(A, s, o->seed, sk_prec, ft.SA, ft.ld, ft.sk, ft.err, st, &launches));
     const double ms_sk = t_sk.stop();
     EventTimer t_qr(st);
     const long long spin = o->spin_limit;
-    if (o->factor_prec == CSLS_PREC_F64) {
-        CSLS_TRY(qr_factor_f64((double*)ft.SA, ft.ld, s, n, ft.qr, ft.err, spin, st, &launches));
+    if (o->factor_prec == CSLS_PREC_F64 || o->factor_prec == CSLS_PREC_F64_EMU) {
+        if (o->factor_prec == CSLS_PREC_F64)
+            CSLS_TRY(qr_factor_f64((double*)ft.SA, ft.ld, s, n, ft.qr, ft.err, spin, st, &launches));
+        else
+            CSLS_TRY(qr_factor_f64_emu((double*)ft.SA, ft.ld, s, n, ft.qr, ft.emu, ft.emu_bytes, ft.err, spin, st,
+                                       &launches));
         CSLS_TRY(qr_extract_r_f64((const double*)ft.SA, ft.ld, n, (double*)fp.R, ft.stats, st));
         CSLS_TRY(diag_block_inverses_f64((const double*)fp.R, n, fp.Dinv, st));
     } else {
@@ -481,7 +495,8 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
     csls_factor_t* F = new (std::nothrow) csls_factor_t;
     if (!F) return CSLS_ERR_ARG;
     F->m = A->m; F->n = n; F->nnz = A->nnz; F->s = s; F->r = r;
-    F->variant = o->variant; F->prec = o->factor_prec;
+    F->variant = o->variant;
+    F->prec = o->factor_prec == CSLS_PREC_F32 ? CSLS_PREC_F32 : CSLS_PREC_F64;   // storage type of R
     F->R = fp.R; F->Dinv = fp.Dinv; F->P = fp.P; F->AT = fp.AT;
     F->rdiag_min = stats[0]; F->rdiag_max = stats[1];
     F->nblocks = ceil_div(n, kTrsvBlock);

@@ -180,6 +180,11 @@ int qr_factor_f64(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch&
                   long long spin_limit, cudaStream_t st, int64_t* launches);
 int qr_factor_f32(float* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, int* err,
                   long long spin_limit, cudaStream_t st, int64_t* launches);
+// The same factorisation with the trailing-update products emulated exactly on the bf16
+// tensor cores (digit splitting, int64 fixed-point trailing matrix); needs emu scratch.
+size_t qr_emu_scratch_bytes(int64_t s, int64_t n);
+int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, void* emu_work,
+                      size_t emu_bytes, int* err, long long spin, cudaStream_t st, int64_t* launches);
 // R (n x n, ld n, non-negative diagonal, zero below) from the factored matrix; stats[0..2] =
 // min |R_jj|, max |R_jj|, count of zero or non-finite diagonal entries.
 int qr_extract_r_f64(const double* A, int64_t lda, int64_t n, double* R, double* stats, cudaStream_t st);

@@ -621,6 +621,40 @@ static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScrat
     return CSLS_OK;
 }
 
+int qr_panel_launch_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, const QrScratch& q, int* err,
+                        long long spin, cudaStream_t st) {
+    static bool attr_set = false;
+    const size_t smem_cap = 200 * 1024;
+    if (!attr_set) {
+        CSLS_CUDA(cudaFuncSetAttribute(k_panel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_cap));
+        attr_set = true;
+    }
+    const int64_t L = s - j0;
+    int G = panel_grid(L);
+    int64_t chunk = ceil_div(L, G);
+    size_t smem = (size_t)chunk * nbw * sizeof(double);
+    double* tau = q.tau;
+    double* Tm = q.T;
+    double* part = q.partials;
+    long long spin_ll = spin;
+    void* args[] = {&A, (void*)&lda, (void*)&s, (void*)&j0, (void*)&nbw, (void*)&chunk, &tau, &Tm, &part,
+                    (void*)&q.bar, &spin_ll, &err};
+    if (smem <= smem_cap)
+        CSLS_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel<double, true>, dim3(G), dim3(kPanelThreads), args,
+                                              smem, st));
+    else
+        CSLS_CUDA(cudaLaunchCooperativeKernel((const void*)k_panel<double, false>, dim3(G), dim3(kPanelThreads), args,
+                                              0, st));
+    return CSLS_OK;
+}
+
+int qr_wreduce_launch_f64(const QrScratch& q, int ks, int nbw, int64_t nprime, cudaStream_t st) {
+    k_wreduce<double><<<(unsigned)ceil_div(nprime, 256), 256, 0, st>>>(q.Wp, ks, q.T, nbw, q.Wn, nprime);
+    CSLS_CUDA(cudaGetLastError());
+    return CSLS_OK;
+}
+
 int qr_factor_f64(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, int* err, long long spin,
                   cudaStream_t st, int64_t* launches) {
     return qr_factor_impl<double>(A, lda, s, n, q, err, spin, st, launches);

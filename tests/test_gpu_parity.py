@@ -311,3 +311,33 @@ def test_f32_factor_guard(csls):
     assert _anorm_rel(Ad, x.cpu().numpy(), xo) <= max(1e-9, 4 * _anorm_rel(Ad, x_hh, xo))
     rep2 = csls.csls_solve(F, A, torch.tensor(p.b[0], device="cuda"), guard_cond=1.0001, raise_on_error=False)[1]
     assert rep2["status"] == 6
+
+
+# ----------------------------------------------------------------------------- emulated FP64 trailing updates
+
+def test_emulated_factor_matches_oracle_well_conditioned(csls):
+    rng = np.random.default_rng(21)
+    A = random_sparse(3000, 200, 12, rng)   # 7 panels (ragged), several row chunks
+    Re = csls.csls_factor(dev(csls, A), s=800, seed=9, prec="f64emu").R().cpu().numpy()
+    Ro = oracle.factor(A, 800, 9)["R"]
+    assert _rel(Re, Ro) < 1e-10
+    assert np.all(np.diag(Re) >= 0) and np.all(np.tril(Re, -1) == 0)
+
+
+@pytest.mark.parametrize("case", ["cfg1", "ragged_rfm"])
+def test_emulated_factor_rfm_backward_error_and_solve(csls, case):
+    p = SKETCH_CASES[case]()
+    s = min(4 * p.n, p.m)
+    F = csls.csls_factor(dev(csls, p), seed=11, prec="f64emu")
+    R = F.R().cpu().numpy()
+    h, d = oracle.hash_rows(p.m, s, 11)
+    SA = oracle.sketch(p, s, h, d)
+    err = np.linalg.norm(R.T @ R - SA.T @ SA) / np.linalg.norm(SA) ** 2
+    assert err < 1e-11
+    b = p.b[0]
+    x, rep = csls.csls_solve(F, dev(csls, p), torch.tensor(b, device="cuda"))
+    Ad = p.dense()
+    _, xo, _ = oracle.csqrp_lsqr(p, b, seed=11)
+    x_hh, _ = oracle.hhqr_solve(Ad, b)
+    assert _anorm_rel(Ad, x.cpu().numpy(), xo) <= max(1e-10, 2 * _anorm_rel(Ad, x_hh, xo))
+    assert rep["istop"] in (1, 2) and rep["cond_est"] < 10
