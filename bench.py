@@ -22,7 +22,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solve time to rel. error 1e-10 (sketch+QR+LSQR); SpMV-pair HBM GB/s vs peak"
-WORKLOAD = "2D Poisson RFM, 8x8 boxes, J=200 tanh features, 30x30 points/box, m=65280 n=12800 nnz=14.4M, s=4n"
+WORKLOADS = {
+    "cfg2": "2D Poisson RFM, 8x8 boxes, J=200 tanh features, 30x30 points/box, m=65280 n=12800 nnz=14.4M, s=4n",
+    "cfg1": "2D Poisson RFM, 2x2 boxes, J=100, 20x20 points/box, m=1920 n=400 nnz=208k, s=4n",
+    "cfg3": "3D Poisson RFM, 4x4x4 boxes, J=400, 12^3 points/box, m=134784 n=25600 nnz=58.06M, s=4n",
+    "cfg4a": "2D Poisson RFM cfg2 matrix with 64 right-hand sides sin(a pi x) sin(b pi y), block LSQR, s=4n",
+    "cfg5": "random sparse 2e6 x 2e4, 10/row, columns scaled over 10 decades, s=4n",
+    "rfm6x6": "2D Poisson RFM, 6x6 boxes, J=200, 30x30 points/box, m=36720 n=7200 nnz=8.06M, s=4n",
+}
+WORKLOAD = WORKLOADS["cfg2"]
 
 
 def parse():
@@ -134,6 +142,8 @@ def oracle_sample_seconds(p, s, iters_full):
 
 
 def run_reference(args):
+    global WORKLOAD
+    WORKLOAD = WORKLOADS.get(args.config, args.config)
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
@@ -184,8 +194,10 @@ def main():
         p = config_problem(args.config)
     m, n, nnz = p.m, p.n, p.nnz
     s = 4 * n
+    global WORKLOAD
+    WORKLOAD = WORKLOADS.get(args.config, args.config)
     A = csls.Csr.from_numpy(p.row_ptr, p.col, p.val, m, n)
-    b = torch.tensor(p.b[0], device="cuda")
+    b = torch.tensor(p.b[0] if p.nrhs == 1 else p.b, device="cuda")   # cfg4a: 64 right-hand sides
     opts = dict(seed=1, prec=args.prec, tol=1e-12)
     stream = torch.cuda.current_stream()
 
@@ -237,7 +249,8 @@ def main():
         torch.cuda.synchronize()
         Ap = torch.sparse_csr_tensor(A.row_ptr, A.col.to(torch.int64), A.val, (m, n))
         dx = xp - x
-        rel_a = float(torch.linalg.vector_norm(torch.mv(Ap, dx)) / torch.linalg.vector_norm(torch.mv(Ap, xp)))
+        dx2, xp2 = dx.reshape(-1, n).t(), xp.reshape(-1, n).t()
+        rel_a = float(torch.linalg.matrix_norm(Ap @ dx2) / torch.linalg.matrix_norm(Ap @ xp2))
         plain = {"dtype": "f64", "s_per_solve": p0.elapsed_time(p1) / 1e3, "iterations": int(repp["iterations"]),
                  "status": csls.STATUS_NAMES.get(repp["status"], repp["status"]),
                  "factor_ms": Fp.report["ms_factor"], "solve_ms": repp["ms_solve"],
@@ -267,10 +280,10 @@ def main():
     h_row = torch.tensor(p.row_ptr).pin_memory()
     h_col = torch.tensor(p.col).pin_memory()
     h_val = torch.tensor(p.val).pin_memory()
-    h_b = torch.tensor(p.b[0]).pin_memory()
-    h_x = torch.empty(n, dtype=torch.float64).pin_memory()
+    h_b = (torch.tensor(p.b[0]) if p.nrhs == 1 else torch.tensor(p.b)).pin_memory()
+    h_x = torch.empty(tuple(b.shape[:-1]) + (n,), dtype=torch.float64).pin_memory()
     h2d = h_row.numel() * 8 + h_col.numel() * 4 + h_val.numel() * 8 + h_b.numel() * 8
-    d2h = n * 8
+    d2h = h_x.numel() * 8
     torch.cuda.synchronize()
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(1, min(args.steps, 2))
@@ -295,6 +308,27 @@ def main():
     # about 2.1 TFLOP/s only on integer-valued operands); cuBLAS DGEMM measures 1.10 on the same part.
     fp64_peak = 1100.0
     qr_gflops = qr_flops(s, n) / (statistics.median(qr_ms) * 1e-3) / 1e9
+    if args.prec == "f64emu":
+        # the trailing-update products run as 21 exact bf16 digit-pair products each: report the bf16
+        # tensor work executed per second against the measured dense bf16 peak
+        pairs = 21
+        ach = pairs * qr_gflops / 1e3
+        roofline = {"bound": "tensor", "kernel": "qr: FP64 panels + trailing-update products as exact bf16 digit "
+                    "products (mma.sync m16n8k16)", "achieved": ach, "peak": bf16, "unit": "TFLOP/s (bf16)",
+                    "frac": ach / bf16, "traffic": None, "peak_source": src + " bf16 (MEASURED_PEAKS.json); the "
+                    "legacy mma.sync pipe measures ~605 TFLOP/s on this part",
+                    "fp64_equivalent_tflops": qr_gflops / 1e3}
+    elif args.prec == "f64":
+        roofline = {"bound": "tensor", "kernel": "qr: panels + DMMA f64 trailing update", "achieved": qr_gflops / 1e3,
+                    "peak": fp64_peak / 1e3, "unit": "TFLOP/s", "frac": qr_gflops / fp64_peak, "traffic": None,
+                    "peak_source": "measured DMMA m16n8k16 f64 rate with full-mantissa operands (1.10 TFLOP/s, "
+                                   "= cuBLAS DGEMM); bf16 x nominal fp64/bf16 ratio would give %.2f"
+                                   % (bf16 * 1.25 / 2250)}
+    else:
+        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x clock
+        roofline = {"bound": "alu", "kernel": "qr: FP32 FMA panels + trailing update", "achieved": qr_gflops / 1e3,
+                    "peak": alu_peak, "unit": "TFLOP/s", "frac": qr_gflops / 1e3 / alu_peak, "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
     cpu = None
     if rank == 0:
         total, sample, spent = oracle_sample_seconds(p, s, int(statistics.median(iters)))
@@ -313,14 +347,7 @@ def main():
             "status": csls.STATUS_NAMES.get(status, status), "iterations": int(statistics.median(iters)),
             "phase_ms": {"sketch": statistics.median(sketch_ms), "factor": statistics.median(qr_ms),
                          "solve": statistics.median(solve_ms)},
-            "roofline": {"bound": "tensor", "kernel": "qr (panel + trailing update, %s)" % (
-                             "DMMA f64" if args.prec == "f64" else
-                             "exact bf16 digit products on mma.sync" if args.prec == "f64emu" else "FP32 FMA"),
-                         "achieved": qr_gflops / 1e3, "peak": fp64_peak / 1e3, "unit": "TFLOP/s (FP64-equivalent)",
-                         "frac": qr_gflops / fp64_peak, "traffic": None,
-                         "peak_source": "measured DMMA m16n8k16 f64 rate with full-mantissa operands (1.10 TFLOP/s, "
-                                        "= cuBLAS DGEMM); bf16 x nominal fp64/bf16 ratio would give %.2f"
-                                        % (bf16 * 1.25 / 2250)},
+            "roofline": roofline,
             "spmv_pair": {"bound": "hbm", "achieved": pair_gbs, "peak": hbm, "unit": "GB/s", "frac": pair_gbs / hbm,
                           "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src},
             "cpu_baseline": cpu,

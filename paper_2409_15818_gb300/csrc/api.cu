@@ -12,6 +12,11 @@
 namespace csls {
 
 size_t backward_ws_bytes(int64_t m, int64_t n, int64_t nb);
+size_t block_ws_bytes(int64_t m, int64_t n, int64_t nb, int64_t nrhs);
+int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb, double* x,
+                int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep, cudaStream_t st,
+                int64_t* launches);
+constexpr int64_t kBlockMax = 64;   // right-hand sides per block pass
 
 // ------------------------------------------------------------------ validation kernel
 
@@ -578,7 +583,10 @@ int csls_solve_workspace(const csls_factor_t* F, int64_t nrhs, size_t* bytes) {
     if (!F || !bytes || nrhs <= 0) return CSLS_ERR_ARG;
     Carve c{nullptr, 0, 0, true};
     solve_carve(c, F);
-    *bytes = c.off;
+    size_t need = c.off;
+    if (nrhs > 1 && F->variant == CSLS_VARIANT_QR)
+        need = std::max(need, block_ws_bytes(F->m, F->n, F->nblocks, std::min(nrhs, kBlockMax)));
+    *bytes = need;
     return CSLS_OK;
 }
 
@@ -597,13 +605,27 @@ int csls_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64
     EventTimer t(st);
     int64_t launches = 0, max_it = 0;
     int status = CSLS_OK;
-    for (int64_t k = 0; k < nrhs; ++k) {
-        csls_report rk{};
-        int sk = solve_one(F, A, b + k * ldb, x + k * ldx, o, w, &rk, st, &launches);
-        if (k == 0 && rep) *rep = rk;
-        max_it = std::max<int64_t>(max_it, rk.iterations);
-        if (status == CSLS_OK && sk != CSLS_OK) status = sk;
-        if (sk == CSLS_ERR_CUDA || sk == CSLS_ERR_TIMEOUT) break;
+    if (nrhs > 1 && F->variant == CSLS_VARIANT_QR) {
+        // block form: independent recurrences sharing each pass over A and R
+        for (int64_t k0 = 0; k0 < nrhs; k0 += kBlockMax) {
+            const int64_t nk = std::min(kBlockMax, nrhs - k0);
+            csls_report rk{};
+            int sk = block_solve(F, A, b + k0 * ldb, nk, ldb, x + k0 * ldx, ldx, o, work, work_bytes, &rk, st,
+                                 &launches);
+            if (k0 == 0 && rep) *rep = rk;
+            max_it = std::max<int64_t>(max_it, rk.iterations);
+            if (status == CSLS_OK && sk != CSLS_OK) status = sk;
+            if (sk == CSLS_ERR_CUDA || sk == CSLS_ERR_TIMEOUT) break;
+        }
+    } else {
+        for (int64_t k = 0; k < nrhs; ++k) {
+            csls_report rk{};
+            int sk = solve_one(F, A, b + k * ldb, x + k * ldx, o, w, &rk, st, &launches);
+            if (k == 0 && rep) *rep = rk;
+            max_it = std::max<int64_t>(max_it, rk.iterations);
+            if (status == CSLS_OK && sk != CSLS_OK) status = sk;
+            if (sk == CSLS_ERR_CUDA || sk == CSLS_ERR_TIMEOUT) break;
+        }
     }
     const double ms = t.stop();
     if (rep) {

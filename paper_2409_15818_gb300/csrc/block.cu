@@ -1,0 +1,557 @@
+// Block form of the LSQR solve for many right-hand sides of one A: nrhs
+// independent Paige-Saunders recurrences (one LsqrState per column) that share
+// every pass over A, A^T and R. Vectors are stored row-major (n x W, W = nrhs
+// rounded up to 8, padded columns start converged), so SpMM gathers one 8W-byte
+// row per nonzero and the triangular solves become 64 x 64 by 64 x 8 block
+// products. The triangular solves keep the single-RHS chain structure (tickets,
+// per-block flags with bounded waits), with 8 right-hand sides per CTA so the
+// chain of one column group stays short while all groups run side by side.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "lsqr.cuh"
+
+namespace csls {
+
+constexpr int kBT = 256;       // threads
+constexpr int kNR = 8;         // right-hand sides per triangular-solve CTA
+constexpr int kTB = kTrsvBlock;
+
+struct BlockCtl {
+    TrsvCtl up, lo;
+    unsigned spmv_cnt, all_done, iter_launched, pad;
+};
+
+__device__ __forceinline__ bool col_live(const LsqrState* st, int c) { return !*(volatile const int*)&st[c].done; }
+
+// ------------------------------------------------------------------ start: U = B (column-major in), beta_1
+
+__global__ void __launch_bounds__(kBT) k_blk_start(const double* B, int64_t ldb, int64_t m, int nrhs, int W, double* U,
+                                                   LsqrState* st, BlockCtl* ctl, double* partials) {
+    extern __shared__ double red[];   // [kBT/32][W]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double sq[2] = {0.0, 0.0};
+    for (int64_t i = (blockIdx.x * (int64_t)kBT + threadIdx.x) >> 5; i < m; i += ((int64_t)gridDim.x * kBT) >> 5) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c < W) {
+                const double v = c < nrhs ? B[(int64_t)c * ldb + i] : 0.0;
+                U[i * W + c] = v;
+                sq[h] += v * v;
+            }
+        }
+    }
+    for (int h = 0; h < 2; ++h)
+        if (lane + 32 * h < W) red[warp * W + lane + 32 * h] = sq[h];
+    __syncthreads();
+    for (int c = threadIdx.x; c < W; c += kBT) {
+        double t = 0.0;
+        for (int w = 0; w < kBT / 32; ++w) t += red[w * W + c];
+        partials[(int64_t)blockIdx.x * W + c] = t;
+    }
+    if (last_cta(&ctl->spmv_cnt, gridDim.x)) {
+        for (int c = threadIdx.x; c < W; c += kBT) {
+            double t = 0.0;
+            for (unsigned q = 0; q < gridDim.x; ++q) t += __ldcg(partials + (int64_t)q * W + c);
+            const double beta = sqrt(t);
+            LsqrState* s = st + c;
+            s->beta = beta;
+            s->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+            s->bnorm = beta;
+            s->phibar = beta;
+            s->rnorm = beta;
+            if (!isfinite(beta)) { set_error(&s->err, CSLS_ERR_NONFINITE); s->done = 1; }
+            if (beta == 0.0) { s->done = 1; s->istop = 3; }
+        }
+        if (threadIdx.x == 0) ctl->spmv_cnt = 0;
+    }
+}
+
+// ------------------------------------------------------------------ U = A Z - (alpha/beta) U  (per column), beta
+
+__global__ void __launch_bounds__(kBT) k_blk_spmm(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                  const double* __restrict__ val, int64_t m, int W,
+                                                  const double* __restrict__ Z, double* U, LsqrState* st,
+                                                  BlockCtl* ctl, double* partials) {
+    extern __shared__ double red[];   // [kBT/32][W] then coef[W]
+    double* coef = red + (kBT / 32) * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = threadIdx.x; c < W; c += kBT)
+        coef[c] = col_live(st, c) ? st[c].alpha / st[c].beta : 0.0;
+    __syncthreads();
+    double sq[2] = {0.0, 0.0};
+    for (int64_t i = (blockIdx.x * (int64_t)kBT + threadIdx.x) >> 5; i < m; i += ((int64_t)gridDim.x * kBT) >> 5) {
+        double acc[2] = {0.0, 0.0};
+        const int64_t pe = rp[i + 1];
+        for (int64_t p = rp[i]; p < pe; ++p) {
+            const double a = __ldg(val + p);
+            const double* zr = Z + (int64_t)__ldg(col + p) * W;
+            acc[0] += a * (lane < W ? zr[lane] : 0.0);
+            if (lane + 32 < W) acc[1] += a * zr[lane + 32];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c < W) {
+                const double un = acc[h] - coef[c] * U[i * W + c];
+                U[i * W + c] = un;
+                sq[h] += un * un;
+            }
+        }
+    }
+    __syncthreads();
+    for (int h = 0; h < 2; ++h)
+        if (lane + 32 * h < W) red[warp * W + lane + 32 * h] = sq[h];
+    __syncthreads();
+    for (int c = threadIdx.x; c < W; c += kBT) {
+        double t = 0.0;
+        for (int w = 0; w < kBT / 32; ++w) t += red[w * W + c];
+        partials[(int64_t)blockIdx.x * W + c] = t;
+    }
+    if (last_cta(&ctl->spmv_cnt, gridDim.x)) {
+        for (int c = threadIdx.x; c < W; c += kBT) {
+            if (!col_live(st, c)) continue;
+            double t = 0.0;
+            for (unsigned q = 0; q < gridDim.x; ++q) t += __ldcg(partials + (int64_t)q * W + c);
+            const double beta = sqrt(t);
+            st[c].beta = beta;
+            st[c].inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+            if (!isfinite(beta)) { set_error(&st[c].err, CSLS_ERR_NONFINITE); st[c].done = 1; }
+        }
+        if (threadIdx.x == 0) ctl->spmv_cnt = 0;
+    }
+}
+
+// G = A^T U diag(1/beta)
+__global__ void __launch_bounds__(kBT) k_blk_spmtm(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                   const double* __restrict__ val, int64_t n, int W,
+                                                   const double* __restrict__ U, double* G, const LsqrState* st) {
+    extern __shared__ double scale[];   // [W]
+    const int lane = threadIdx.x & 31;
+    for (int c = threadIdx.x; c < W; c += kBT) scale[c] = col_live(st, c) ? st[c].inv_beta : 0.0;
+    __syncthreads();
+    for (int64_t j = (blockIdx.x * (int64_t)kBT + threadIdx.x) >> 5; j < n; j += ((int64_t)gridDim.x * kBT) >> 5) {
+        double acc[2] = {0.0, 0.0};
+        const int64_t pe = rp[j + 1];
+        for (int64_t p = rp[j]; p < pe; ++p) {
+            const double a = __ldg(val + p);
+            const double* ur = U + (int64_t)__ldg(col + p) * W;
+            acc[0] += a * (lane < W ? ur[lane] : 0.0);
+            if (lane + 32 < W) acc[1] += a * ur[lane + 32];
+        }
+        if (lane < W) G[j * W + lane] = acc[0] * scale[lane];
+        if (lane + 32 < W) G[j * W + lane + 32] = acc[1] * scale[lane + 32];
+    }
+}
+
+// ------------------------------------------------------------------ block triangular solves
+
+__device__ __forceinline__ bool wait_flag_b(const int* flag, int want, long long spin, int* err) {
+    long long it = 0;
+    while (ld_acquire(flag) != want) {
+        if (++it > spin) { set_error(err, CSLS_ERR_TIMEOUT); return false; }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+// Z = R^{-1} (V diag(1/alpha)) for the live columns, with the x / wx epilogue.
+// CTA = (ticket k) -> block row b = nb - 1 - k / ngroups, column group g = k % ngroups.
+template <class TR>
+__global__ void __launch_bounds__(kBT)
+k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const double* __restrict__ Dinv, int W,
+                 const double* V, double* Z, double* WX, double* X, int* flags, BlockCtl* ctl, LsqrState* st,
+                 long long spin, int* err) {
+    __shared__ int tk_s;
+    __shared__ unsigned epoch_s;
+    __shared__ double rhs[kTB][kNR];
+    __shared__ double cf[kNR][4];   // 1/alpha, cx, cw, first (0 for converged columns)
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        epoch_s = *(volatile unsigned*)&ctl->up.epoch;
+        tk_s = (int)atomicAdd(&ctl->up.ticket, 1u);
+    }
+    __syncthreads();
+    const int b = nb - 1 - tk_s / ngroups, grp = tk_s % ngroups;
+    const int c0g = grp * kNR;
+    if (tid < kNR) {
+        const int c = c0g + tid;
+        const bool live = col_live(st, c);
+        cf[tid][0] = live ? 1.0 / st[c].alpha : 0.0;
+        cf[tid][1] = st[c].cx;
+        cf[tid][2] = st[c].cw;
+        cf[tid][3] = live ? (double)st[c].first : -1.0;
+    }
+    const int want = (int)(epoch_s + 1u);
+    const int64_t r0 = (int64_t)b * kTB;
+    const int bs = (int)(n - r0 < kTB ? n - r0 : kTB);
+    const int row = tid & (kTB - 1), cp = tid >> 6;    // columns c0g + 2cp, +1
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int c = nb - 1; c > b; --c) {
+        const int64_t cc0 = (int64_t)c * kTB;
+        const int cs = (int)(n - cc0 < kTB ? n - cc0 : kTB);
+        if (tid == 0) wait_flag_b(&flags[(int64_t)c * ngroups + grp], want, spin, err);
+        __syncthreads();
+        if (row < bs) {
+            const TR* rp = R + (r0 + row) + cc0 * n;
+            const double* zp = Z + cc0 * W + c0g + 2 * cp;
+            for (int k = 0; k < cs; ++k) {
+                const double r = (double)__ldg(rp + (int64_t)k * n);
+                const double2 zz = __ldcg(reinterpret_cast<const double2*>(zp + (int64_t)k * W));
+                acc0 += r * zz.x;
+                acc1 += r * zz.y;
+            }
+        }
+    }
+    __syncthreads();
+    if (row < bs) {
+        rhs[row][2 * cp] = V[(r0 + row) * W + c0g + 2 * cp] * cf[2 * cp][0] - acc0;
+        rhs[row][2 * cp + 1] = V[(r0 + row) * W + c0g + 2 * cp + 1] * cf[2 * cp + 1][0] - acc1;
+    } else {
+        rhs[row][2 * cp] = 0.0;
+        rhs[row][2 * cp + 1] = 0.0;
+    }
+    __syncthreads();
+    const double* D = Dinv + (int64_t)b * kTB * kTB;
+    double z0 = 0.0, z1 = 0.0;
+    for (int k = 0; k < kTB; ++k) {
+        const double d = D[row + k * kTB];
+        z0 += d * rhs[k][2 * cp];
+        z1 += d * rhs[k][2 * cp + 1];
+    }
+    if (row < bs) {
+        const int64_t base = (r0 + row) * W + c0g + 2 * cp;
+        Z[base] = z0;
+        Z[base + 1] = z1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int lc = 2 * cp + h;
+            const double first = cf[lc][3];
+            if (first < 0.0) continue;   // converged column: x and w stay as they are
+            const double zk = h == 0 ? z0 : z1;
+            if (first != 0.0) {
+                WX[base + h] = zk;
+            } else {
+                const double w = WX[base + h];
+                X[base + h] += cf[lc][1] * w;
+                WX[base + h] = zk - cf[lc][2] * w;
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        st_release(&flags[(int64_t)b * ngroups + grp], want);
+        const unsigned prev = atomicAdd(&ctl->up.done, 1u);
+        if (prev == (unsigned)(nb * ngroups) - 1) {
+            for (int c = 0; c < W; ++c) st[c].first = 0;
+            ctl->up.ticket = 0;
+            ctl->up.done = 0;
+            __threadfence();
+            atomicAdd(&ctl->up.epoch, 1u);
+        }
+    }
+}
+
+// MODE 2 (start): V = R^{-T} G, alpha_1. MODE 1: V = R^{-T} G - (beta/alpha) V, alpha, scalar steps.
+// The solve runs in place in G. CTA = (ticket k) -> block b = k / ngroups, group g = k % ngroups.
+template <class TR, int MODE>
+__global__ void __launch_bounds__(kBT)
+k_blk_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const double* __restrict__ Dinv, int W,
+                 double* G, double* V, int* flags, BlockCtl* ctl, LsqrState* st, double* partials, double* hist,
+                 long long spin, int* err) {
+    __shared__ int tk_s;
+    __shared__ unsigned epoch_s;
+    __shared__ double rhs[kTB][kNR];
+    __shared__ double coef[kNR];
+    __shared__ double red[4][kNR];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        epoch_s = *(volatile unsigned*)&ctl->lo.epoch;
+        tk_s = (int)atomicAdd(&ctl->lo.ticket, 1u);
+    }
+    __syncthreads();
+    const int b = tk_s / ngroups, grp = tk_s % ngroups;
+    const int c0g = grp * kNR;
+    if (tid < kNR) {
+        const int c = c0g + tid;
+        coef[tid] = (MODE == 1 && col_live(st, c)) ? st[c].beta / st[c].alpha : 0.0;
+    }
+    const int want = (int)(epoch_s + 1u);
+    const int64_t r0 = (int64_t)b * kTB;
+    const int bs = (int)(n - r0 < kTB ? n - r0 : kTB);
+    const int colr = tid & (kTB - 1), cp = tid >> 6;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int c = 0; c < b; ++c) {
+        const int64_t cc0 = (int64_t)c * kTB;
+        if (tid == 0) wait_flag_b(&flags[(int64_t)c * ngroups + grp], want, spin, err);
+        __syncthreads();
+        if (colr < bs) {
+            const TR* rp = R + cc0 + (r0 + colr) * n;   // column r0 + colr, rows cc0 .. cc0 + 63
+            const double* gp = G + cc0 * W + c0g + 2 * cp;
+            for (int k = 0; k < kTB; ++k) {
+                const double r = (double)__ldg(rp + k);
+                const double2 gg = __ldcg(reinterpret_cast<const double2*>(gp + (int64_t)k * W));
+                acc0 += r * gg.x;
+                acc1 += r * gg.y;
+            }
+        }
+    }
+    __syncthreads();
+    if (colr < bs) {
+        rhs[colr][2 * cp] = G[(r0 + colr) * W + c0g + 2 * cp] - acc0;
+        rhs[colr][2 * cp + 1] = G[(r0 + colr) * W + c0g + 2 * cp + 1] - acc1;
+    } else {
+        rhs[colr][2 * cp] = 0.0;
+        rhs[colr][2 * cp + 1] = 0.0;
+    }
+    __syncthreads();
+    const double* D = Dinv + (int64_t)b * kTB * kTB;
+    double z0 = 0.0, z1 = 0.0;
+    for (int k = 0; k < kTB; ++k) {
+        const double d = D[k + colr * kTB];
+        z0 += d * rhs[k][2 * cp];
+        z1 += d * rhs[k][2 * cp + 1];
+    }
+    double sq0 = 0.0, sq1 = 0.0;
+    if (colr < bs) {
+        const int64_t base = (r0 + colr) * W + c0g + 2 * cp;
+        G[base] = z0;
+        G[base + 1] = z1;
+        const double v0 = MODE == 1 ? z0 - coef[2 * cp] * V[base] : z0;
+        const double v1 = MODE == 1 ? z1 - coef[2 * cp + 1] * V[base + 1] : z1;
+        V[base] = v0;
+        V[base + 1] = v1;
+        sq0 = v0 * v0;
+        sq1 = v1 * v1;
+    }
+    // per-column sums over the block's 64 rows: reduce inside the 64-thread group of each column pair
+    for (int o = 16; o > 0; o >>= 1) {
+        sq0 += __shfl_xor_sync(0xffffffffu, sq0, o);
+        sq1 += __shfl_xor_sync(0xffffffffu, sq1, o);
+    }
+    __shared__ double wred[kBT / 32][2];
+    if ((tid & 31) == 0) { wred[tid >> 5][0] = sq0; wred[tid >> 5][1] = sq1; }
+    __syncthreads();
+    if (tid < 4) {   // column pair tid: warps 2 tid, 2 tid + 1
+        red[tid][0] = wred[2 * tid][0] + wred[2 * tid + 1][0];
+        red[tid][1] = wred[2 * tid][1] + wred[2 * tid + 1][1];
+        partials[(int64_t)b * W + c0g + 2 * tid] = red[tid][0];
+        partials[(int64_t)b * W + c0g + 2 * tid + 1] = red[tid][1];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(&flags[(int64_t)b * ngroups + grp], want);
+    if (last_cta(&ctl->lo.done, (unsigned)(nb * ngroups))) {
+        // one thread per column: reduce its partials in block order, then its scalar step
+        int live = 0;
+        for (int c = tid; c < W; c += kBT) {
+            if (!col_live(st, c)) continue;
+            double t = 0.0;
+            for (int q = 0; q < nb; ++q) t += __ldcg(partials + (int64_t)q * W + c);
+            const double alpha_new = sqrt(t);
+            if (MODE == 1) {
+                lsqr_scalar_step(st + c, alpha_new, c == 0 ? hist : nullptr);
+            } else {
+                st[c].alpha = alpha_new;
+                st[c].rhobar = alpha_new;
+                if (c == 0 && hist) hist[0] = alpha_new;
+                if (alpha_new == 0.0 || !isfinite(alpha_new)) {
+                    st[c].done = 1;
+                    st[c].istop = 3;
+                    if (!isfinite(alpha_new)) set_error(&st[c].err, CSLS_ERR_NONFINITE);
+                }
+            }
+            live += st[c].done ? 0 : 1;
+        }
+        const int nlive = __syncthreads_count(live > 0);
+        if (tid == 0) {
+            ctl->all_done = nlive == 0;
+            ctl->lo.ticket = 0;
+            ctl->lo.done = 0;
+            __threadfence();
+            atomicAdd(&ctl->lo.epoch, 1u);
+        }
+    }
+}
+
+// x_c += cx_c wx_c for the columns that ran at least one iteration; write x (column-major, ldx).
+__global__ void k_blk_finish(const double* X, const double* WX, int64_t n, int W, int nrhs, const LsqrState* st,
+                             double* x, int64_t ldx) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nrhs;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / n);
+        const int64_t i = idx % n;
+        double v = X[i * W + c];
+        if (st[c].iter > 0) v += st[c].cx * WX[i * W + c];
+        x[(int64_t)c * ldx + i] = v;
+    }
+}
+
+// ------------------------------------------------------------------ host driver
+
+struct BlockWs {
+    BlockCtl* ctl;
+    LsqrState* st;
+    double *U, *V, *Z, *G, *WX, *X, *sp_part, *lo_part, *hist;
+    int *flags_up, *flags_lo, *err;
+    int64_t hist_cap;
+    int W;
+};
+
+static BlockWs block_carve(Carve& c, int64_t m, int64_t n, int64_t nb, int64_t nrhs) {
+    BlockWs w;
+    w.W = (int)round_up(nrhs, kNR);
+    const int64_t W = w.W;
+    w.ctl = c.take<BlockCtl>(1);
+    w.st = c.take<LsqrState>((size_t)W);
+    w.U = c.take<double>((size_t)(m * W));
+    w.V = c.take<double>((size_t)(n * W));
+    w.Z = c.take<double>((size_t)(n * W));
+    w.G = c.take<double>((size_t)(n * W));
+    w.WX = c.take<double>((size_t)(n * W));
+    w.X = c.take<double>((size_t)(n * W));
+    w.sp_part = c.take<double>((size_t)((int64_t)device_sm_count() * 8 * W + 64));
+    w.lo_part = c.take<double>((size_t)(nb * W + 64));
+    w.hist_cap = n + 4;
+    w.hist = c.take<double>((size_t)(2 * (w.hist_cap + 2)));
+    w.flags_up = c.take<int>((size_t)(nb * (W / kNR)));
+    w.flags_lo = c.take<int>((size_t)(nb * (W / kNR)));
+    w.err = c.take<int>(1);
+    return w;
+}
+
+size_t block_ws_bytes(int64_t m, int64_t n, int64_t nb, int64_t nrhs) {
+    Carve c{nullptr, 0, 0, true};
+    block_carve(c, m, n, nb, nrhs);
+    return c.off;
+}
+
+int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb, double* x,
+                int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep, cudaStream_t st,
+                int64_t* launches) {
+    if (F->variant != CSLS_VARIANT_QR) return CSLS_ERR_ARG;
+    if (nrhs > 64) return CSLS_ERR_ARG;
+    const int64_t m = F->m, n = F->n, nb = F->nblocks;
+    Carve c{(char*)work, 0, bytes, false};
+    BlockWs w = block_carve(c, m, n, nb, nrhs);
+    const int W = w.W, ngroups = W / kNR;
+    const long long spin = o->spin_limit;
+    std::vector<LsqrState> h((size_t)W);
+    for (int k = 0; k < W; ++k) {
+        LsqrState s{};
+        s.atol = o->atol;
+        s.btol = o->btol;
+        s.maxit = o->maxit > 0 ? o->maxit : n;
+        s.fixed = o->fixed_iters;
+        s.hist_cap = w.hist_cap;
+        s.cs2 = -1.0;
+        s.first = 1;
+        h[(size_t)k] = s;
+    }
+    CSLS_CUDA(cudaMemcpyAsync(w.st, h.data(), sizeof(LsqrState) * (size_t)W, cudaMemcpyHostToDevice, st));
+    CSLS_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(BlockCtl), st));
+    CSLS_CUDA(cudaMemsetAsync(w.flags_up, 0, sizeof(int) * (size_t)(nb * ngroups), st));
+    CSLS_CUDA(cudaMemsetAsync(w.flags_lo, 0, sizeof(int) * (size_t)(nb * ngroups), st));
+    CSLS_CUDA(cudaMemsetAsync(w.X, 0, sizeof(double) * (size_t)(n * W), st));
+    CSLS_CUDA(cudaMemsetAsync(w.Z, 0, sizeof(double) * (size_t)(n * W), st));
+    CSLS_CUDA(cudaMemsetAsync(w.V, 0, sizeof(double) * (size_t)(n * W), st));
+    CSLS_CUDA(cudaMemsetAsync(w.G, 0, sizeof(double) * (size_t)(n * W), st));
+    CSLS_CUDA(cudaMemsetAsync(w.WX, 0, sizeof(double) * (size_t)(n * W), st));
+    CSLS_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    const int sms = device_sm_count();
+    const int gm = (int)std::min<int64_t>(ceil_div(m * 32, kBT), (int64_t)sms * 8);
+    const int gn = (int)std::min<int64_t>(ceil_div(n * 32, kBT), (int64_t)sms * 8);
+    const size_t red_bytes = sizeof(double) * (size_t)((kBT / 32) * W + W);
+    const dim3 tg((unsigned)(nb * ngroups));
+    auto upper = [&]() -> int {
+        if (F->prec == CSLS_PREC_F64)
+            k_blk_trsv_upper<double><<<tg, kBT, 0, st>>>((const double*)F->R, n, (int)nb, ngroups, F->Dinv, W, w.V,
+                                                         w.Z, w.WX, w.X, w.flags_up, w.ctl, w.st, spin, w.err);
+        else
+            k_blk_trsv_upper<float><<<tg, kBT, 0, st>>>((const float*)F->R, n, (int)nb, ngroups, F->Dinv, W, w.V, w.Z,
+                                                        w.WX, w.X, w.flags_up, w.ctl, w.st, spin, w.err);
+        CSLS_CUDA(cudaGetLastError());
+        return CSLS_OK;
+    };
+    auto lower = [&](int mode) -> int {
+        if (F->prec == CSLS_PREC_F64) {
+            if (mode == 1)
+                k_blk_trsv_lower<double, 1><<<tg, kBT, 0, st>>>((const double*)F->R, n, (int)nb, ngroups, F->Dinv, W,
+                                                                w.G, w.V, w.flags_lo, w.ctl, w.st, w.lo_part, w.hist,
+                                                                spin, w.err);
+            else
+                k_blk_trsv_lower<double, 2><<<tg, kBT, 0, st>>>((const double*)F->R, n, (int)nb, ngroups, F->Dinv, W,
+                                                                w.G, w.V, w.flags_lo, w.ctl, w.st, w.lo_part, w.hist,
+                                                                spin, w.err);
+        } else {
+            if (mode == 1)
+                k_blk_trsv_lower<float, 1><<<tg, kBT, 0, st>>>((const float*)F->R, n, (int)nb, ngroups, F->Dinv, W,
+                                                               w.G, w.V, w.flags_lo, w.ctl, w.st, w.lo_part, w.hist,
+                                                               spin, w.err);
+            else
+                k_blk_trsv_lower<float, 2><<<tg, kBT, 0, st>>>((const float*)F->R, n, (int)nb, ngroups, F->Dinv, W,
+                                                               w.G, w.V, w.flags_lo, w.ctl, w.st, w.lo_part, w.hist,
+                                                               spin, w.err);
+        }
+        CSLS_CUDA(cudaGetLastError());
+        return CSLS_OK;
+    };
+    k_blk_start<<<gm, kBT, red_bytes, st>>>(b, ldb, m, (int)nrhs, W, w.U, w.st, w.ctl, w.sp_part);
+    CSLS_CUDA(cudaGetLastError());
+    k_blk_spmtm<<<gn, kBT, sizeof(double) * W, st>>>(F->AT.row_ptr, F->AT.col, F->AT.val, n, W, w.U, w.G, w.st);
+    CSLS_CUDA(cudaGetLastError());
+    CSLS_TRY(lower(2));
+    int64_t nl = 3;
+    const int64_t limit = o->fixed_iters > 0 ? o->fixed_iters : (o->maxit > 0 ? o->maxit : n);
+    const int64_t chunk = o->check_every > 0 ? o->check_every : 16;
+    for (int64_t it = 0; it < limit; it += chunk) {
+        for (int64_t k = 0; k < chunk && it + k < limit; ++k) {
+            CSLS_TRY(upper());
+            k_blk_spmm<<<gm, kBT, red_bytes, st>>>(A->row_ptr, A->col, A->val, m, W, w.Z, w.U, w.st, w.ctl, w.sp_part);
+            CSLS_CUDA(cudaGetLastError());
+            k_blk_spmtm<<<gn, kBT, sizeof(double) * W, st>>>(F->AT.row_ptr, F->AT.col, F->AT.val, n, W, w.U, w.G,
+                                                             w.st);
+            CSLS_CUDA(cudaGetLastError());
+            CSLS_TRY(lower(1));
+            nl += 4;
+        }
+        BlockCtl hc{};
+        CSLS_CUDA(cudaMemcpyAsync(&hc, w.ctl, sizeof(BlockCtl), cudaMemcpyDeviceToHost, st));
+        CSLS_CUDA(cudaStreamSynchronize(st));
+        if (hc.all_done) break;
+    }
+    k_blk_finish<<<(unsigned)std::min<int64_t>(ceil_div(n * nrhs, 256), (int64_t)sms * 8), 256, 0, st>>>(
+        w.X, w.WX, n, W, (int)nrhs, w.st, x, ldx);
+    CSLS_CUDA(cudaGetLastError());
+    ++nl;
+    std::vector<LsqrState> out((size_t)W);
+    int err = 0;
+    CSLS_CUDA(cudaMemcpyAsync(out.data(), w.st, sizeof(LsqrState) * (size_t)W, cudaMemcpyDeviceToHost, st));
+    CSLS_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CSLS_CUDA(cudaStreamSynchronize(st));
+    int status = err;
+    int64_t max_it = 0;
+    for (int64_t k = 0; k < nrhs; ++k) {
+        const LsqrState& s = out[(size_t)k];
+        max_it = std::max<int64_t>(max_it, s.iter);
+        if (status == CSLS_OK && s.err) status = s.err;
+        if (status == CSLS_OK && o->fixed_iters <= 0 && s.istop == 0 && s.done) status = CSLS_ERR_NOT_CONVERGED;
+    }
+    if (rep) {
+        const LsqrState& s = out[0];
+        rep->istop = s.istop;
+        rep->iterations = max_it;
+        rep->bnorm = s.bnorm;
+        rep->rnorm = s.rnorm;
+        rep->arnorm = s.arnorm;
+        rep->anorm = std::sqrt(s.anorm2);
+        rep->ynorm = s.ynorm;
+    }
+    if (launches) *launches += nl;
+    return status;
+}
+
+}  // namespace csls

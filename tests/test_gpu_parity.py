@@ -176,15 +176,39 @@ def test_fixed_iterations_track_oracle(csls):
         assert _rel(x.cpu().numpy(), xo) < 1e-10
 
 
-def test_multi_rhs_equals_single(csls):
-    p = poisson2d(3, 2, 37, 11, 9, R=1.5, seed=7, modes=((1, 1), (2, 1), (1, 3)))
+def test_multi_rhs_block_matches_single_and_oracle(csls):
+    """The block form (independent recurrences sharing the passes over A and R)
+    gives each column the single-right-hand-side result up to rounding, and
+    matches the oracle; 19 columns exercise a ragged last group of 8."""
+    modes = tuple((a, c) for a in range(1, 6) for c in range(1, 5))[:19]
+    p = poisson2d(3, 2, 37, 11, 9, R=1.5, seed=7, modes=modes)
     A = dev(csls, p)
     F = csls.csls_factor(A, seed=3)
     B = torch.tensor(p.b, device="cuda")
     X, rep = csls.csls_solve(F, A, B)
-    for k in range(3):
-        xk, _ = csls.csls_solve(F, A, B[k])
-        assert torch.equal(X[k], xk)
+    assert X.shape == (19, p.n)
+    Ad = p.dense()
+    fac = oracle.factor(p, min(4 * p.n, p.m), 3)
+    for k in (0, 7, 8, 18):
+        xk, repk = csls.csls_solve(F, A, B[k])
+        assert _anorm_rel(Ad, X[k].cpu().numpy(), xk.cpu().numpy()) < 1e-12
+        xo, info = oracle.lsqr(p, p.b[k], fac["R"], "qr")
+        x_hh, _ = oracle.hhqr_solve(Ad, p.b[k])
+        assert _anorm_rel(Ad, X[k].cpu().numpy(), xo) <= max(1e-10, 2 * _anorm_rel(Ad, x_hh, xo))
+    assert rep["iterations"] >= repk["iterations"]
+
+
+def test_multi_rhs_fixed_iterations_track_single(csls):
+    rng = np.random.default_rng(27)
+    A = random_sparse(3000, 150, 10, rng, scale_exp=3.0)
+    Bn = rng.standard_normal((10, 3000))
+    F = csls.csls_factor(dev(csls, A), s=600, seed=5)
+    B = torch.tensor(Bn, device="cuda")
+    X, rep = csls.csls_solve(F, dev(csls, A), B, fixed_iters=6)
+    fac = oracle.factor(A, 600, 5)
+    for k in range(10):
+        xo, _ = oracle.lsqr(A, Bn[k], fac["R"], "qr", fixed_iters=6)
+        assert _rel(X[k].cpu().numpy(), xo) < 1e-10
 
 
 def test_svd_variant_rank_deficient(csls):
