@@ -83,6 +83,23 @@ __device__ __forceinline__ void hmma(float (&c)[4], const uint32_t (&a)[4], cons
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Four 8x8 b16 matrices from shared memory in the mma.sync fragment order; `row` is this
+// lane's row address.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* row) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
 // ------------------------------------------------------------------ setup kernels
 
 // E_c = exponent bound of column c of SA: 2^E_c > ||SA(:, c)||_2 >= every |entry| at any later stage.
@@ -227,14 +244,17 @@ __global__ void k_wdigits(const double* Wn, int64_t nprime, int64_t ldw, unsigne
 
 constexpr int kVtcCols = 64;
 constexpr int kVtcPad = 8;                     // bf16 elements of padding per k-row
-constexpr int kVtcLdk = kVtcStep + kVtcPad;    // 136
+constexpr int kVtcLdk = kVtcStep + kVtcPad;    // 40
 
 struct VtcSmem {
-    unsigned short As[kDig][kPanel][kVtcLdk];   // V^T digits: [p][a][k]
-    unsigned short Bs[kDig][kVtcCols][kVtcLdk]; // C digits:   [q][c][k]
+    unsigned short As[2][kDig][kPanel][kVtcLdk];   // V^T digits, two pipeline stages: [p][a][k]
+    long long Craw[2][kVtcCols][kVtcStep];        // raw fixed-point C rows, two stages: [c][k]
+    unsigned short Bs[kDig][kVtcCols][kVtcLdk];    // C digits of the current step: [q][c][k]
 };
 
 // Wp[chunk](a, c) for c in the column tile: sum over the chunk's rows of V(r, a) C(r, c).
+// Two-stage cp.async pipeline: the V^T digits and raw C rows of step k + 1 are in flight
+// while step k is cut into digits and multiplied.
 __global__ void __launch_bounds__(kEmuThreads, 2)
 k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int nbw, int64_t kc,
           const unsigned short* VTd, int64_t ldv, const int* ecol, const int* E, double* Wp, int64_t nprime) {
@@ -248,53 +268,51 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
     const int64_t le = lb + kc < L ? lb + kc : L;
     const int mi = warp & 1, nt = warp >> 1;                   // warp: a in mi*16.., cols nt*16..
     // Per output, the level sums are packed into two int64 fixed-point words:
-    // hi = sum_{l<3} T_l 2^(8 (2 - l)), lo = sum_{l>=3} T_l 2^(8 (5 - l)); per K-step each T_l < 2^24,
+    // hi = sum_{l<3} T_l 2^(8 (2 - l)), lo = sum_{l>=3} T_l 2^(8 (5 - l)); per K-step each T_l < 2^22,
     // so both stay below 2^50 over 1600 steps.
     long long hi[2][4], lo[2][4];
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
         for (int h = 0; h < 4; ++h) { hi[j][h] = 0; lo[j][h] = 0; }
-    // each thread stages the same 8 C entries (column c = tid / 4, rows 8 (tid % 4) .. + 8) of every
-    // 32-row step; the next step's entries are loaded before this step's products run
-    constexpr int kPer = kVtcCols * kVtcStep / kEmuThreads;   // 8
-    const int sc_c = tid / (kVtcStep / kPer), sc_k = (tid % (kVtcStep / kPer)) * kPer;
-    const int64_t sc_gc = jc + c0 + sc_c;
-    const bool sc_ok = sc_gc < n;
-    const long long* sc_col = Cfix + sc_gc * lda + j0;
-    long long cnext[kPer];
-#pragma unroll
-    for (int e = 0; e < kPer; ++e) {
-        const int64_t lr = lb + sc_k + e;
-        cnext[e] = (sc_ok && lr < le) ? sc_col[lr] : 0LL;
-    }
+
+    auto issue = [&](int stage, int64_t k0) {
+        // V^T digits: per (p, a) 32 contiguous bf16 = 4 chunks of 16 B
+        for (int idx = tid; idx < kDig * kPanel * 4; idx += kEmuThreads) {
+            const int ch = idx & 3, a = (idx >> 2) % kPanel, p = (idx >> 2) / kPanel;
+            const int64_t lr = k0 + ch * 8;
+            const bool ok = lr < ldv;
+            const unsigned short* src = VTd + ((int64_t)p * kPanel + a) * ldv + (ok ? lr : 0);
+            cp_async16(&sm.As[stage][p][a][ch * 8], src, ok ? 16 : 0);
+        }
+        // raw C: per column 32 rows = 16 chunks of two int64
+        for (int idx = tid; idx < kVtcCols * (kVtcStep / 2); idx += kEmuThreads) {
+            const int ch = idx % (kVtcStep / 2), c = idx / (kVtcStep / 2);
+            const int64_t lr = k0 + 2 * ch, gc = jc + c0 + c;
+            const int rows = (gc < n) ? (int)(le - lr < 0 ? 0 : (le - lr > 2 ? 2 : le - lr)) : 0;
+            const long long* src = Cfix + (rows > 0 ? (j0 + lr) + gc * lda : 0);
+            cp_async16(&sm.Craw[stage][c][2 * ch], src, rows * 8);
+        }
+        cp_async_commit();
+    };
+
+    int stage = 0;
+    issue(0, lb);
     for (int64_t k0 = lb; k0 < le; k0 += kVtcStep) {
-        // stage V^T digits (zero beyond the chunk)
-        for (int idx = tid; idx < kDig * kPanel * (kVtcStep / 2); idx += kEmuThreads) {
-            const int kk = (idx % (kVtcStep / 2)) * 2;
-            const int a = (idx / (kVtcStep / 2)) % kPanel;
-            const int p = idx / (kVtcStep / 2) / kPanel;
-            const int64_t lr = k0 + kk;
-            uint32_t w = 0;
-            if (lr + 1 < le) {
-                w = *reinterpret_cast<const uint32_t*>(VTd + ((int64_t)p * kPanel + a) * ldv + lr);
-            } else if (lr < le) {
-                w = VTd[((int64_t)p * kPanel + a) * ldv + lr];
+        if (k0 + kVtcStep < le) issue(stage ^ 1, k0 + kVtcStep);
+        else cp_async_commit();                                // keep the group count uniform
+        cp_async_wait<1>();
+        __syncthreads();
+        // cut this step's C entries into digits (each thread: one column, 8 rows)
+        {
+            const int c = tid >> 2, kq = (tid & 3) * 8;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                int d[kDig];
+                digits_fix(sm.Craw[stage][c][kq + e], d);
+#pragma unroll
+                for (int q = 0; q < kDig; ++q) sm.Bs[q][c][kq + e] = bf16_of_int(d[q]);
             }
-            *reinterpret_cast<uint32_t*>(&sm.As[p][a][kk]) = w;
-        }
-        // C digits of this step from the prefetched entries, then prefetch the next step
-#pragma unroll
-        for (int e = 0; e < kPer; ++e) {
-            int d[kDig];
-            digits_fix(cnext[e], d);
-#pragma unroll
-            for (int q = 0; q < kDig; ++q) sm.Bs[q][sc_c][sc_k + e] = bf16_of_int(d[q]);
-        }
-#pragma unroll
-        for (int e = 0; e < kPer; ++e) {
-            const int64_t lr = k0 + kVtcStep + sc_k + e;
-            cnext[e] = (sc_ok && lr < le) ? sc_col[lr] : 0LL;
         }
         __syncthreads();
 #pragma unroll
@@ -305,20 +323,12 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
                 const int q = l - p;
 #pragma unroll
                 for (int ks = 0; ks < kVtcStep; ks += 16) {
-                    uint32_t af[4], bfr[2][2];
-                    const int ar = mi * 16 + g;
-                    af[0] = *reinterpret_cast<const uint32_t*>(&sm.As[p][ar][ks + 2 * t]);
-                    af[1] = *reinterpret_cast<const uint32_t*>(&sm.As[p][ar + 8][ks + 2 * t]);
-                    af[2] = *reinterpret_cast<const uint32_t*>(&sm.As[p][ar][ks + 2 * t + 8]);
-                    af[3] = *reinterpret_cast<const uint32_t*>(&sm.As[p][ar + 8][ks + 2 * t + 8]);
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int bc = nt * 16 + j * 8 + g;
-                        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&sm.Bs[q][bc][ks + 2 * t]);
-                        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&sm.Bs[q][bc][ks + 2 * t + 8]);
-                    }
-                    hmma(acc[0], af, bfr[0]);
-                    hmma(acc[1], af, bfr[1]);
+                    uint32_t af[4], bq[4];
+                    ldsm_x4(af, &sm.As[stage][p][mi * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
+                    ldsm_x4(bq, &sm.Bs[q][nt * 16 + (lane & 7) + ((lane >> 4) & 1) * 8][ks + ((lane >> 3) & 1) * 8]);
+                    const uint32_t b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
+                    hmma(acc[0], af, b0);
+                    hmma(acc[1], af, b1);
                 }
             }
 #pragma unroll
@@ -331,8 +341,10 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
                 }
         }
         __syncthreads();
+        stage ^= 1;
     }
-    // W(a, c) = 2^(e_a + E_c - 14) sum_l 2^(-8 l) T_l   (C entries carry scale 2^(E_c - 39))
+    cp_async_wait<0>();
+    // W(a, c) = 2^(e_a + E_c - 14) sum_l 2^(-8 l) T_l   (C entries carry scale 2^(E_c - 47))
     double* out = Wp + (int64_t)blockIdx.y * kPanel * nprime;
 #pragma unroll
     for (int j = 0; j < 2; ++j)
@@ -384,29 +396,26 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
                 const int64_t col = cb + wn * 16 + j * 8 + 2 * t + (h & 1);
                 cval[i][j][h] = (lr < L && col < nprime) ? Cfix[(j0 + lr) + (jc + col) * lda] : 0LL;
             }
-    for (int idx = tid; idx < kDig * kUpdRows * (kPanel / 2); idx += kEmuThreads) {
-        const int a2 = (idx % (kPanel / 2)) * 2;
-        const int r = (idx / (kPanel / 2)) % kUpdRows;
-        const int p = idx / (kPanel / 2) / kUpdRows;
+    // digit tiles: each row of 32 bf16 is 4 chunks of 16 B
+    for (int idx = tid; idx < kDig * kUpdRows * 4; idx += kEmuThreads) {
+        const int ch = idx & 3, r = (idx >> 2) % kUpdRows, p = (idx >> 2) / kUpdRows;
         const int64_t lr = rb + r;
-        uint32_t w = 0;
-        if (lr < L) w = *reinterpret_cast<const uint32_t*>(Vd + ((int64_t)p * ldv + lr) * kPanel + a2);
-        *reinterpret_cast<uint32_t*>(&sm.Vs[p][r][a2]) = w;
+        const bool ok = lr < L;
+        cp_async16(&sm.Vs[p][r][ch * 8], Vd + ((int64_t)p * ldv + (ok ? lr : 0)) * kPanel + ch * 8, ok ? 16 : 0);
     }
-    for (int idx = tid; idx < kDig * kUpdCols * (kPanel / 2); idx += kEmuThreads) {
-        const int a2 = (idx % (kPanel / 2)) * 2;
-        const int c = (idx / (kPanel / 2)) % kUpdCols;
-        const int q = idx / (kPanel / 2) / kUpdCols;
+    for (int idx = tid; idx < kDig * kUpdCols * 4; idx += kEmuThreads) {
+        const int ch = idx & 3, c = (idx >> 2) % kUpdCols, q = (idx >> 2) / kUpdCols;
         const int64_t col = cb + c;
-        uint32_t w = 0;
-        if (col < nprime) w = *reinterpret_cast<const uint32_t*>(Wd + ((int64_t)q * ldw + col) * kPanel + a2);
-        *reinterpret_cast<uint32_t*>(&sm.Ws[q][c][a2]) = w;
+        const bool ok = col < nprime;
+        cp_async16(&sm.Ws[q][c][ch * 8], Wd + ((int64_t)q * ldw + (ok ? col : 0)) * kPanel + ch * 8, ok ? 16 : 0);
     }
+    cp_async_commit();
     for (int i = tid; i < kUpdRows; i += kEmuThreads) sm.frow[i] = rb + i < L ? frow[rb + i] : 0;
     for (int i = tid; i < kUpdCols; i += kEmuThreads) {
         sm.gcol[i] = cb + i < nprime ? gcol[cb + i] : 0;
         sm.ecol[i] = cb + i < nprime ? E[jc + cb + i] : 0;
     }
+    cp_async_wait<0>();
     __syncthreads();
     long long acc64[2][2][4];
 #pragma unroll 1
@@ -422,21 +431,12 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
             const int q = l - p;
 #pragma unroll
             for (int ks = 0; ks < kPanel; ks += 16) {
-                uint32_t af[2][4], bfr[2][2];
+                uint32_t af[2][4], bq[4];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int r = wm * 32 + i * 16 + g;
-                    af[i][0] = *reinterpret_cast<const uint32_t*>(&sm.Vs[p][r][ks + 2 * t]);
-                    af[i][1] = *reinterpret_cast<const uint32_t*>(&sm.Vs[p][r + 8][ks + 2 * t]);
-                    af[i][2] = *reinterpret_cast<const uint32_t*>(&sm.Vs[p][r][ks + 2 * t + 8]);
-                    af[i][3] = *reinterpret_cast<const uint32_t*>(&sm.Vs[p][r + 8][ks + 2 * t + 8]);
-                }
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int c = wn * 16 + j * 8 + g;
-                    bfr[j][0] = *reinterpret_cast<const uint32_t*>(&sm.Ws[q][c][ks + 2 * t]);
-                    bfr[j][1] = *reinterpret_cast<const uint32_t*>(&sm.Ws[q][c][ks + 2 * t + 8]);
-                }
+                for (int i = 0; i < 2; ++i)
+                    ldsm_x4(af[i], &sm.Vs[p][wm * 32 + i * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
+                ldsm_x4(bq, &sm.Ws[q][wn * 16 + (lane & 7) + ((lane >> 4) & 1) * 8][ks + ((lane >> 3) & 1) * 8]);
+                const uint32_t bfr[2][2] = {{bq[0], bq[1]}, {bq[2], bq[3]}};
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
