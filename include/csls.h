@@ -215,6 +215,31 @@ int csls_solve_backward(const csls_factor_t* factor, const csls_csr* A, const do
                         const csls_opts* opts, void* work, size_t work_bytes, csls_report* rep,
                         csls_stream_t stream);
 
+/* ---------------------------------------------------------------- batches */
+/* Many independent problems of uneven size, each with its own factor (built by
+ * csls_factor): all LSQR recurrences advance together in batched kernels whose
+ * grids cover every instance, and the whole iteration runs as ONE CUDA-graph
+ * launch -- a WHILE conditional node repeats one batched iteration until every
+ * instance has met its stopping rule or limit (the loop condition is set on the
+ * device). Each instance computes the same recurrence as csls_solve (single
+ * right-hand side, QR variant). A[i], b[i] (m_i) and x[i] (n_i) are device arrays;
+ * reps (host, count entries, may be NULL) is filled after a stream sync.
+ * The call creates and destroys one capture stream and one graph per call. */
+int csls_batch_solve_workspace(int64_t count, const csls_factor_t* const* factors, size_t* bytes);
+int csls_batch_solve(int64_t count, const csls_factor_t* const* factors, const csls_csr* A,
+                     const double* const* b, double* const* x, const csls_opts* opts, void* work,
+                     size_t work_bytes, csls_report* reps, csls_stream_t stream);
+
+/* Autotuner for the SpMV pair: times A x and A^T u with 4, 8, 16 and 32 threads
+ * per row (CUDA events, 5 runs each) on this matrix and stores the fastest
+ * choices in the factor (used by csls_batch_solve). Workspace: 16 (m + n) + 1024
+ * bytes. group, group_t and ms[2] (best times) may be NULL. */
+int csls_autotune_spmv(csls_factor_t* factor, const csls_csr* A, void* work, size_t work_bytes, int* group,
+                       int* group_t, float* ms, csls_stream_t stream);
+/* Set the SpMV threads-per-row choices directly (4, 8, 16 or 32), e.g. from a
+ * persisted autotuning cache. */
+int csls_factor_set_spmv_groups(csls_factor_t* factor, int group, int group_t);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,13 @@ EXPORTS = {
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                   ctypes.c_void_p, ctypes.c_void_p]),
     "csls_backward_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "csls_batch_solve_workspace": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "csls_batch_solve": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "csls_autotune_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "csls_factor_set_spmv_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "csls_solve_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
@@ -321,6 +328,63 @@ def csls_solve_backward(F, A, b, x, grad_x, want_b=True, want_val=True, opts=Non
                                       _ptr(work), work.numel(), ctypes.byref(rep), _stream(stream)),
            "csls_solve_backward")
     return gb, gv, rep.as_dict()
+
+
+# --------------------------------------------------------------------------- batches and autotuning
+
+def csls_batch_solve(factors, As, bs, opts=None, stream=None, raise_on_error=True, **kw):
+    """Solve many independent problems (each with its own factor) in one CUDA-graph
+    launch; returns (list of x, list of report dicts)."""
+    opts = opts or make_opts(**kw)
+    count = len(factors)
+    handles = (ctypes.c_void_p * count)(*[f.handle.value for f in factors])
+    csrs = (csls_csr * count)(*[A.struct() for A in As])
+    bs = [b.contiguous() for b in bs]
+    xs = [torch.empty(A.n, dtype=torch.float64, device=b.device) for A, b in zip(As, bs)]
+    bp = (ctypes.c_void_p * count)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * count)(*[x.data_ptr() for x in xs])
+    nbytes = ctypes.c_size_t()
+    _check(_lib().csls_batch_solve_workspace(count, handles, ctypes.byref(nbytes)), "csls_batch_solve_workspace")
+    work = _workspace(nbytes.value, bs[0].device)
+    reps = (csls_report * count)()
+    st = _lib().csls_batch_solve(count, handles, csrs, bp, xp, ctypes.byref(opts), _ptr(work), work.numel(), reps,
+                                 _stream(stream))
+    if raise_on_error:
+        _check(st, "csls_batch_solve")
+    return xs, [r.as_dict() for r in reps], st
+
+
+def _tune_key(A):
+    return "%dx%d:%d:%s" % (A.m, A.n, A.nnz, torch.cuda.get_device_name(A.val.device))
+
+
+def csls_autotune(F, A, cache=None, stream=None):
+    """Pick the SpMV threads-per-row for A x and A^T u by timing the candidates on
+    this matrix (csls_autotune_spmv); with `cache` (a JSON path) the choice is
+    looked up first and stored after tuning. Returns (group, group_t)."""
+    import json
+    key = _tune_key(A)
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+    if key in table:
+        g, gt = table[key]
+        _check(_lib().csls_factor_set_spmv_groups(F.handle, int(g), int(gt)), "csls_factor_set_spmv_groups")
+        return int(g), int(gt)
+    work = _workspace(16 * (A.m + A.n) + 1024, A.val.device)
+    g, gt = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_float * 2)()
+    a = A.struct()
+    _check(_lib().csls_autotune_spmv(F.handle, ctypes.byref(a), _ptr(work), work.numel(), ctypes.byref(g),
+                                     ctypes.byref(gt), ms, _stream(stream)), "csls_autotune_spmv")
+    if cache:
+        table[key] = [g.value, gt.value]
+        tmp = cache + ".%d.tmp" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return g.value, gt.value
 
 
 # --------------------------------------------------------------------------- autograd

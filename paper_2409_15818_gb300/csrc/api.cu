@@ -185,44 +185,6 @@ static ApplyWs apply_carve(Carve& c, const csls_factor_t* F) {
 
 // ------------------------------------------------------------------ host helpers
 
-// Extreme singular values of the (k+1) x k lower bidiagonal (alpha_1..alpha_k on the
-// diagonal, beta_2..beta_{k+1} below) from bisection on the tridiagonal B^T B.
-static double bidiag_cond(const std::vector<double>& alpha, const std::vector<double>& beta) {
-    const size_t k = alpha.size();
-    if (k == 0) return 0.0;
-    std::vector<double> d(k), e(k > 0 ? k - 1 : 0);
-    for (size_t i = 0; i < k; ++i) d[i] = alpha[i] * alpha[i] + beta[i] * beta[i];
-    for (size_t i = 0; i + 1 < k; ++i) e[i] = alpha[i + 1] * beta[i];
-    double lo = 0.0, hi = 0.0;
-    for (size_t i = 0; i < k; ++i) {
-        double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0);
-        hi = std::max(hi, d[i] + r);
-    }
-    auto count_below = [&](double x) {   // Sturm count of eigenvalues < x
-        int cnt = 0;
-        double q = d[0] - x;
-        if (q < 0) ++cnt;
-        for (size_t i = 1; i < k; ++i) {
-            double qq = q != 0.0 ? q : 1e-300;
-            q = d[i] - x - e[i - 1] * e[i - 1] / qq;
-            if (q < 0) ++cnt;
-        }
-        return cnt;
-    };
-    auto kth = [&](int idx) {   // idx-th smallest eigenvalue (0-based)
-        double a = lo, b = hi;
-        for (int it = 0; it < 200; ++it) {
-            double mid = 0.5 * (a + b);
-            if (count_below(mid) > idx) b = mid; else a = mid;
-            if (b - a <= 1e-15 * b) break;
-        }
-        return 0.5 * (a + b);
-    };
-    const double lmin = kth(0), lmax = kth((int)k - 1);
-    if (!(lmin > 0.0)) return INFINITY;
-    return std::sqrt(lmax / lmin);
-}
-
 static int read_err(const int* derr, cudaStream_t st) {
     int e = 0;
     CSLS_CUDA(cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -265,6 +227,8 @@ static int solve_one(const csls_factor_t* F, const csls_csr* A, const double* b,
     *launches += 4;
     const int64_t limit = o->fixed_iters > 0 ? o->fixed_iters : h.maxit;
     const int64_t chunk = o->check_every > 0 ? o->check_every : 16;
+    const bool guarded = F->prec == CSLS_PREC_F32 && o->guard_cond > 0 && o->fixed_iters <= 0;
+    int64_t next_guard = 32;
     for (int64_t it = 0; it < limit + 1; it += chunk) {
         for (int64_t k = 0; k < chunk && it + k < limit; ++k) {
             if (F->variant == CSLS_VARIANT_QR)
@@ -285,6 +249,16 @@ static int solve_one(const csls_factor_t* F, const csls_csr* A, const double* b,
         CSLS_CUDA(cudaStreamSynchronize(st));
         if (done) break;
         if (it + chunk >= limit) break;
+        const int64_t k_now = std::min<int64_t>(it + chunk, w.hist_cap);
+        if (guarded && k_now >= next_guard) {
+            // early guard: the bidiagonal's cond only grows with k, so once it passes the
+            // guard the binary32 factor is rejected without running to the iteration limit
+            std::vector<double> hh((size_t)(2 * (k_now + 1) + 2));
+            CSLS_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, st));
+            CSLS_CUDA(cudaStreamSynchronize(st));
+            if (!(bidiag_cond_hist(hh.data(), k_now) < o->guard_cond)) break;
+            next_guard *= 4;
+        }
     }
     k_final_x<<<grid_small(n), 256, 0, st>>>(x, w.wx, n, w.st);
     CSLS_CUDA(cudaGetLastError());
@@ -295,12 +269,7 @@ static int solve_one(const csls_factor_t* F, const csls_csr* A, const double* b,
     std::vector<double> hh((size_t)(2 * (kk + 1) + 2));
     CSLS_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, st));
     CSLS_CUDA(cudaStreamSynchronize(st));
-    std::vector<double> al((size_t)kk), be((size_t)kk);
-    for (int64_t i = 0; i < kk; ++i) {
-        al[(size_t)i] = hh[(size_t)(2 * i)];          // alpha_{i+1}
-        be[(size_t)i] = hh[(size_t)(2 * (i + 1) + 1)];  // beta_{i+2}
-    }
-    const double cond = bidiag_cond(al, be);
+    const double cond = bidiag_cond_hist(hh.data(), kk);
     if (rep) {
         rep->istop = out.istop;
         rep->iterations = out.iter;
@@ -506,6 +475,8 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
     F->rdiag_min = stats[0]; F->rdiag_max = stats[1];
     F->nblocks = ceil_div(n, kTrsvBlock);
     F->a_col = A->col;
+    F->spmv_group = 0;
+    F->spmv_group_t = 0;
     *factor = F;
     return CSLS_OK;
 }

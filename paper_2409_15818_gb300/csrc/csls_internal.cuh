@@ -211,4 +211,6 @@ struct csls_factor_s {
     double rdiag_min, rdiag_max;
     int64_t nblocks;       // ceil(n/64)
     const int32_t* a_col;  // identity of the matrix the factor was built from
+    int spmv_group;        // threads per row for A x (0: heuristic), set by the autotuner
+    int spmv_group_t;      // threads per row for A^T u
 };

@@ -118,6 +118,53 @@ __device__ __forceinline__ void lsqr_scalar_step(LsqrState* st, double alpha_new
     if (stop) st->done = 1;
 }
 
+// Condition number of the (k+1) x k lower bidiagonal B_k of the Golub-Kahan process
+// (alpha_1..alpha_k on the diagonal, beta_2..beta_{k+1} below), read from the LSQR
+// history (hist[2i] = alpha_{i+1}, hist[2i+3] = beta_{i+2}), by Sturm bisection on the
+// tridiagonal B_k^T B_k. The singular values of B_k lie inside those of the
+// preconditioned operator, so the value is a lower bound on cond(A M) that rises
+// toward it with k.
+__host__ __device__ inline double bidiag_cond_hist(const double* hist, long long k) {
+    if (k <= 0) return 0.0;
+    auto al = [&](long long i) { return hist[2 * i]; };
+    auto be = [&](long long i) { return hist[2 * (i + 1) + 1]; };
+    auto dg = [&](long long i) { return al(i) * al(i) + be(i) * be(i); };
+    auto of = [&](long long i) { return al(i + 1) * be(i); };   // (i, i+1) entry of B^T B
+    double hi = 0.0;
+    for (long long i = 0; i < k; ++i) {
+        const double r = (i > 0 ? fabs(of(i - 1)) : 0.0) + (i + 1 < k ? fabs(of(i)) : 0.0);
+        hi = fmax(hi, dg(i) + r);
+    }
+    auto count_below = [&](double x) {
+        long long cnt = 0;
+        double q = dg(0) - x;
+        if (q < 0) ++cnt;
+        for (long long i = 1; i < k; ++i) {
+            const double qq = q != 0.0 ? q : 1e-300;
+            const double e = of(i - 1);
+            q = dg(i) - x - e * e / qq;
+            if (q < 0) ++cnt;
+        }
+        return cnt;
+    };
+    auto kth = [&](long long idx) {
+        double a = 0.0, b = hi;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (a + b);
+            if (count_below(mid) > idx) b = mid; else a = mid;
+            if (b - a <= 1e-15 * b) break;
+        }
+        return 0.5 * (a + b);
+    };
+    const double lmin = kth(0), lmax = kth(k - 1);
+    if (!(lmin > 0.0)) return INFINITY;
+    return sqrt(lmax / lmin);
+}
+
+// Iterations after which a binary32 factor's cond guard is evaluated early (the bound
+// above already exceeds the guard when the factor has lost the preconditioner).
+__host__ __device__ inline bool guard_checkpoint(long long it) { return it == 32 || it == 128; }
+
 // ------------------------------------------------------------------ launchers (solve building blocks)
 
 struct TrsvArgs {
