@@ -56,6 +56,32 @@ def peaks():
     return 6800.0, 1900.0, "fallback"
 
 
+def read_ceiling_gbs():
+    """Streaming-read bandwidth of this GPU (a reduction over 1 GiB, best of 10): the ceiling of
+    a read-only kernel such as SpMV, which the copy figure (reads + writes) does not give."""
+    import torch
+    a = torch.ones(1 << 27, dtype=torch.float64, device="cuda")
+    a.sum()
+    best = float("inf")
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a.sum()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a
+    return (1 << 30) / (best * 1e-3) / 1e9
+
+
+def bf16_sustained():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f).get("bf16_tflops_sustained", 1700.0)
+    return 1700.0
+
+
 class ClockSampler:
     FIELDS = "clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
@@ -275,8 +301,10 @@ def main():
     opts = dict(seed=1, prec=args.prec, tol=1e-12)
     stream = torch.cuda.current_stream()
 
-    def step():
-        F = csls.csls_factor(A, **opts)
+    def step(time_kernels=0):
+        # time_kernels: the factor brackets each launch of its QR kernel families with CUDA
+        # events on its stream (the per-kernel roofline below)
+        F = csls.csls_factor(A, time_kernels=time_kernels, **opts)
         x, rep = csls.csls_solve(F, A, b, raise_on_error=False, **opts)
         return F, x, rep
 
@@ -291,9 +319,14 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
     qr_ms, solve_ms, sketch_ms, iters = [], [], [], []
+    kern_ms, kern_n, kern_flop = [0.0] * 3, [0] * 3, [0.0] * 3
     e0.record(stream)
     for _ in range(args.steps):
-        F, x, rep = step()
+        F, x, rep = step(time_kernels=1)
+        for f in range(3):
+            kern_ms[f] += F.report["kern_ms"][f]
+            kern_n[f] += F.report["kern_launches"][f]
+            kern_flop[f] += F.report["kern_flop"][f]
         launches += F.report["launches"] + rep["launches"]
         qr_ms.append(F.report["ms_factor"])
         sketch_ms.append(F.report["ms_sketch"])
@@ -331,23 +364,40 @@ def main():
                  "rel_diff_A_norm_vs_chosen": rel_a}
         del Fp, xp
 
-    # SpMV pair (A z, A^T u) timed alone, for the HBM roofline of the Krylov step
+    # SpMV pair (A z, A^T u) timed alone, for the HBM roofline of the Krylov step: 20 pairs captured
+    # in a CUDA graph (as the solver issues them: back to back, no host work in between), replayed
     z = torch.randn(n, dtype=torch.float64, device="cuda")
     u = torch.randn(m, dtype=torch.float64, device="cuda")
-    for _ in range(3):
-        csls.csls_spmv(F, A, z)
-        csls.csls_spmv(F, A, u, trans=True)
+    yz = torch.empty(m, dtype=torch.float64, device="cuda")
+    yu = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def pair():
+        csls.csls_spmv(F, A, z, y=yz)
+        csls.csls_spmv(F, A, u, trans=True, y=yu)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        pair()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(20):
+            pair()
+    graph.replay()
     torch.cuda.synchronize()
-    reps = 50
+    reps = 5
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s0.record(stream)
     for _ in range(reps):
-        csls.csls_spmv(F, A, z)
-        csls.csls_spmv(F, A, u, trans=True)
+        graph.replay()
     s1.record(stream)
     torch.cuda.synchronize()
-    pair_ms = s0.elapsed_time(s1) / reps
+    pair_ms = s0.elapsed_time(s1) / (reps * 20)
+    del graph
     hbm, bf16, src = peaks()
+    bf16_sus = bf16_sustained()
+    read_gbs = read_ceiling_gbs()
     pair_gbs = spmv_pair_bytes(m, n, nnz) / (pair_ms * 1e-3) / 1e9
 
     # end to end through the public API with host buffers
@@ -377,32 +427,48 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
-    # roofline of the dominant kernel family: the QR (panel + DMMA trailing update)
-    # GFLOP/s: DMMA m16n8k16 .f64 throughput on GB300 for full-mantissa operands (the same instruction reaches
-    # about 2.1 TFLOP/s only on integer-valued operands); cuBLAS DGEMM measures 1.10 on the same part.
-    fp64_peak = 1100.0
+    # roofline of the dominant kernel: of the factor's three kernel families (Householder panel,
+    # W = V^T C, C -= V W), the one with the most device time over the timed steps, its CUDA-event
+    # time summed over its launches (algorithmic flops per launch / average launch time)
     qr_gflops = qr_flops(s, n) / (statistics.median(qr_ms) * 1e-3) / 1e9
+    fam_names = {"f64emu": ["k_panel (FP64 Householder panel)", "k_emu_vtc (W = V^T C, exact bf16 digit products)",
+                            "k_emu_update (C -= V W, exact bf16 digit products)"],
+                 "f64": ["k_panel (FP64 Householder panel)", "k_vtc_f64 (W = V^T C, DMMA)",
+                         "k_update_f64 (C -= V W, DMMA)"],
+                 "f32": ["k_panel (FP32 Householder panel)", "k_vtc_f32 (W = V^T C, FP32 FMA)",
+                         "k_update_f32 (C -= V W, FP32 FMA)"]}[args.prec]
+    top = max((1, 2), key=lambda f: kern_ms[f])
+    top_s = kern_ms[top] * 1e-3
+    fp64_peak = 1100.0   # GFLOP/s: DMMA m16n8k16 .f64 with full-mantissa operands (= cuBLAS DGEMM on this part)
+    fams = {fam_names[f].split(" ")[0]: {"ms_total": kern_ms[f], "launches": kern_n[f],
+                                        "share_of_factor": kern_ms[f] / max(sum(qr_ms), 1e-9)} for f in range(3)}
     if args.prec == "f64emu":
-        # the trailing-update products run as 21 exact bf16 digit-pair products each: report the bf16
-        # tensor work executed per second against the measured dense bf16 peak
+        # 21 exact bf16 digit-pair products per binary64 product (6 digits, levels p + q <= 5): the
+        # algorithmic bf16 tensor work of the kernel, against the measured dense bf16 rate
         pairs = 21
-        ach = pairs * qr_gflops / 1e3
-        roofline = {"bound": "tensor", "kernel": "qr: FP64 panels + trailing-update products as exact bf16 digit "
-                    "products (mma.sync m16n8k16)", "achieved": ach, "peak": bf16, "unit": "TFLOP/s (bf16)",
-                    "frac": ach / bf16, "traffic": None, "peak_source": src + " bf16 (MEASURED_PEAKS.json); the "
-                    "legacy mma.sync pipe measures ~605 TFLOP/s on this part",
-                    "fp64_equivalent_tflops": qr_gflops / 1e3}
+        ach = pairs * kern_flop[top] / top_s / 1e12
+        peak = bf16_sus
+        roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": src + " bf16 sustained (kernel timed inside a multi-second step)",
+                    "fp64_equivalent_tflops": kern_flop[top] / top_s / 1e12, "launches": kern_n[top],
+                    "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
     elif args.prec == "f64":
-        roofline = {"bound": "tensor", "kernel": "qr: panels + DMMA f64 trailing update", "achieved": qr_gflops / 1e3,
-                    "peak": fp64_peak / 1e3, "unit": "TFLOP/s", "frac": qr_gflops / fp64_peak, "traffic": None,
+        ach = kern_flop[top] / top_s / 1e12
+        roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": fp64_peak / 1e3,
+                    "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e3), "traffic": None,
                     "peak_source": "measured DMMA m16n8k16 f64 rate with full-mantissa operands (1.10 TFLOP/s, "
                                    "= cuBLAS DGEMM); bf16 x nominal fp64/bf16 ratio would give %.2f"
-                                   % (bf16 * 1.25 / 2250)}
+                                   % (bf16 * 1.25 / 2250), "launches": kern_n[top],
+                    "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
     else:
         alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x clock
-        roofline = {"bound": "alu", "kernel": "qr: FP32 FMA panels + trailing update", "achieved": qr_gflops / 1e3,
-                    "peak": alu_peak, "unit": "TFLOP/s", "frac": qr_gflops / 1e3 / alu_peak, "traffic": None,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+        ach = kern_flop[top] / top_s / 1e12
+        roofline = {"bound": "alu", "kernel": fam_names[top], "achieved": ach, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "launches": kern_n[top],
+                    "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
+    roofline["qr_fp64_equivalent_tflops"] = qr_gflops / 1e3
     cpu = None
     if rank == 0:
         total, sample, spent = oracle_sample_seconds(p, s, int(statistics.median(iters)))
@@ -423,7 +489,9 @@ def main():
                          "solve": statistics.median(solve_ms)},
             "roofline": roofline,
             "spmv_pair": {"bound": "hbm", "achieved": pair_gbs, "peak": hbm, "unit": "GB/s", "frac": pair_gbs / hbm,
-                          "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src},
+                          "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src + " copy (read + write)",
+                          "read_only_ceiling": read_gbs, "frac_of_read_ceiling": pair_gbs / read_gbs,
+                          "read_ceiling_source": "torch sum over 1 GiB of fp64 (streaming read), best of 10"},
             "cpu_baseline": cpu,
             "plain_f64_beside": plain,
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -87,10 +87,12 @@ typedef struct {
     double guard_cond;    /* binary32 factor accepted only if estimated cond(A M) < guard_cond */
     int64_t spin_limit;   /* iteration bound for every device spin-wait */
     int64_t check_every;  /* host polls the convergence flag every this many iterations */
+    int64_t time_kernels; /* nonzero: csls_factor brackets each launch of its three QR kernel
+                             families with CUDA events and fills the kern_* report fields */
 } csls_opts;
 
 /* Defaults: gamma 4, s 0, seed 1, QR, F64, rcond 0, atol = btol = 1e-12,
- * maxit 0 (= n), fixed_iters 0, guard_cond 10, spin_limit 2e7, check_every 16. */
+ * maxit 0 (= n), fixed_iters 0, guard_cond 10, spin_limit 2e7, check_every 16, time_kernels 0. */
 void csls_opts_default(csls_opts* opts);
 
 /* Host-side report, filled by csls_factor / csls_solve / csls_solve_backward. */
@@ -108,6 +110,13 @@ typedef struct {
     double rdiag_min, rdiag_max;  /* min / max |R_jj| (QR variant) */
     double ms_sketch, ms_factor, ms_solve;  /* device time per phase (CUDA events) */
     int64_t launches;     /* kernels launched by the call */
+    /* csls_factor with opts->time_kernels: per QR kernel family (0 Householder panel,
+     * 1 W = V^T C product, 2 trailing update C -= V W) the summed CUDA-event time of its
+     * launches, the launch count, and the algorithmic binary64 flops of the products
+     * (2 L n' b per launch for an L x n' trailing matrix and a b-wide panel; 0 for panels). */
+    double kern_ms[3];
+    int64_t kern_launches[3];
+    double kern_flop[3];
 } csls_report;
 
 typedef struct csls_factor_s csls_factor_t;

@@ -39,7 +39,7 @@ class csls_opts(ctypes.Structure):
                 ("variant", ctypes.c_int), ("factor_prec", ctypes.c_int), ("rcond", ctypes.c_double),
                 ("atol", ctypes.c_double), ("btol", ctypes.c_double), ("maxit", ctypes.c_int64),
                 ("fixed_iters", ctypes.c_int64), ("guard_cond", ctypes.c_double), ("spin_limit", ctypes.c_int64),
-                ("check_every", ctypes.c_int64)]
+                ("check_every", ctypes.c_int64), ("time_kernels", ctypes.c_int64)]
 
 
 class csls_report(ctypes.Structure):
@@ -48,10 +48,16 @@ class csls_report(ctypes.Structure):
                 ("rnorm", ctypes.c_double), ("arnorm", ctypes.c_double), ("anorm", ctypes.c_double),
                 ("ynorm", ctypes.c_double), ("cond_est", ctypes.c_double), ("rdiag_min", ctypes.c_double),
                 ("rdiag_max", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_factor", ctypes.c_double),
-                ("ms_solve", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("ms_solve", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("kern_ms", ctypes.c_double * 3), ("kern_launches", ctypes.c_int64 * 3),
+                ("kern_flop", ctypes.c_double * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 EXPORTS = {
@@ -161,7 +167,7 @@ class Csr:
 
 
 def make_opts(gamma=4.0, s=0, seed=1, variant="qr", prec="f64", rcond=0.0, atol=1e-12, btol=1e-12, maxit=0,
-              fixed_iters=0, guard_cond=10.0, spin_limit=20_000_000, check_every=16, tol=None):
+              fixed_iters=0, guard_cond=10.0, spin_limit=20_000_000, check_every=16, time_kernels=0, tol=None):
     o = csls_opts()
     _lib().csls_opts_default(ctypes.byref(o))
     if tol is not None:
@@ -171,6 +177,7 @@ def make_opts(gamma=4.0, s=0, seed=1, variant="qr", prec="f64", rcond=0.0, atol=
     o.rcond, o.atol, o.btol = float(rcond), float(atol), float(btol)
     o.maxit, o.fixed_iters = int(maxit), int(fixed_iters)
     o.guard_cond, o.spin_limit, o.check_every = float(guard_cond), int(spin_limit), int(check_every)
+    o.time_kernels = int(time_kernels)
     return o
 
 
@@ -285,8 +292,9 @@ def csls_precond_apply(F, v, trans=False, stream=None):
     return z
 
 
-def csls_spmv(F, A, x, trans=False, stream=None):
-    y = torch.empty(A.n if trans else A.m, dtype=torch.float64, device=x.device)
+def csls_spmv(F, A, x, trans=False, stream=None, y=None):
+    if y is None:
+        y = torch.empty(A.n if trans else A.m, dtype=torch.float64, device=x.device)
     a = A.struct()
     _check(_lib().csls_spmv(F.handle, ctypes.byref(a), int(bool(trans)), _ptr(x), _ptr(y), _stream(stream)),
            "csls_spmv")

@@ -287,6 +287,30 @@ static int solve_one(const csls_factor_t* F, const csls_csr* A, const double* b,
     return CSLS_OK;
 }
 
+// Per-family QR kernel timing for one csls_factor call (opts->time_kernels).
+struct KtScope {
+    bool on;
+    explicit KtScope(bool o) : on(o) {
+        if (on) kt_install(true);
+    }
+    void collect(csls_report* rep) {
+        if (!on) return;
+        double ms[3], fl[3];
+        int64_t nl[3];
+        kt_collect(ms, nl, fl);
+        on = false;
+        if (rep)
+            for (int f = 0; f < 3; ++f) {
+                rep->kern_ms[f] = ms[f];
+                rep->kern_launches[f] = nl[f];
+                rep->kern_flop[f] = fl[f];
+            }
+    }
+    ~KtScope() {
+        if (on) collect(nullptr);
+    }
+};
+
 struct EventTimer {
     cudaEvent_t a = nullptr, b = nullptr;
     cudaStream_t s;
@@ -345,6 +369,7 @@ void csls_opts_default(csls_opts* o) {
     o->maxit = 0;
     o->fixed_iters = 0;
     o->guard_cond = 10.0;
+    o->time_kernels = 0;
     o->spin_limit = 20000000;
     o->check_every = 16;
 }
@@ -425,6 +450,7 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
     const int sk_prec = o->factor_prec == CSLS_PREC_F32 ? CSLS_PREC_F32 : CSLS_PREC_F64;
     CSLS_TRY(sketch_run(A, s, o->seed, sk_prec, ft.SA, ft.ld, ft.sk, ft.err, st, &launches));
     const double ms_sk = t_sk.stop();
+    KtScope kts(o->time_kernels != 0);
     EventTimer t_qr(st);
     const long long spin = o->spin_limit;
     if (o->factor_prec == CSLS_PREC_F64 || o->factor_prec == CSLS_PREC_F64_EMU) {
@@ -448,6 +474,7 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
                              &launches));
     }
     const double ms_qr = t_qr.stop();
+    kts.collect(rep);
     double stats[4] = {0, 0, 0, 0};
     CSLS_CUDA(cudaMemcpyAsync(stats, ft.stats, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
     e = read_err(ft.err, st);

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kBatT) k_bat_spmv(const InstDesc* inst, const 
         const bool active = i < d.m;
         double acc = 0.0;
         if (MODE == 1 && active)
-            for (int64_t p = d.rp[i] + sub; p < d.rp[i + 1]; p += G) acc += d.val[p] * __ldg(d.z + d.col[p]);
+            acc = row_dot(d.col, d.val, d.z, d.rp[i], d.rp[i + 1], sub, G);
         if (MODE == 1) acc = group_sum_rt(acc, G);
         if (active && sub == 0) {
             const double un = MODE == 1 ? acc - coef_s * d.ut[i] : d.b[i];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kBatT) k_bat_spmtv(const InstDesc* inst, const
         const bool active = j < d.n;
         double acc = 0.0;
         if (active)
-            for (int64_t p = d.rpt[j] + sub; p < d.rpt[j + 1]; p += G) acc += d.valt[p] * __ldg(d.ut + d.colt[p]);
+            acc = row_dot(d.colt, d.valt, d.ut, d.rpt[j], d.rpt[j + 1], sub, G);
         acc = group_sum_rt(acc, G);
         if (active && sub == 0) d.g[j] = acc * scale;
     }
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kBatT) k_tune_spmv(const int64_t* rp, const in
         const int64_t i = base + lane / G;
         double acc = 0.0;
         if (i < rows)
-            for (int64_t p = rp[i] + sub; p < rp[i + 1]; p += G) acc += val[p] * __ldg(x + col[p]);
+            acc = row_dot(col, val, x, rp[i], rp[i + 1], sub, G);
         for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (i < rows && sub == 0) y[i] = acc;
     }

@@ -130,6 +130,15 @@ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 int device_sm_count();
 
+// Optional per-family kernel timing for the factorisation: while timing is on for the
+// calling thread, launch sites bracket their kernels with events on the launching
+// stream; kt_collect sums the intervals once the stream has drained.
+enum { kFamPanel = 0, kFamVtc = 1, kFamUpdate = 2 };
+void kt_install(bool on);
+int kt_begin(int fam, cudaStream_t st);               // token for kt_end; -1 when timing is off
+void kt_end(int token, double flop, cudaStream_t st);
+void kt_collect(double ms[3], int64_t launches[3], double flop[3]);   // call after a stream sync; turns timing off
+
 // ------------------------------------------------------------------ building blocks (host launchers)
 
 // Exclusive scan of `len` int32 counts into out[0..len] (out[len] = total), int64 output.

@@ -68,6 +68,53 @@ __device__ __forceinline__ void xw_update(LsqrState* st, int first, double cx, d
     }
 }
 
+// Partial dot product of one CSR row with x for lane `sub` of a G-lane group (lane
+// sub takes nonzeros sub, sub + G, ...; x is gathered through the read-only path).
+__device__ __forceinline__ double row_dot(const int32_t* __restrict__ col, const double* __restrict__ val,
+                                          const double* __restrict__ x, int64_t pb, int64_t pe, int sub, int G) {
+    double acc = 0.0;
+    for (int64_t p = pb + sub; p < pe; p += G) acc = fma(val[p], __ldg(x + col[p]), acc);
+    return acc;
+}
+
+// The same for long rows with 16-byte loads: after an odd leading nonzero (taken by
+// lane 0), lane sub takes the aligned pairs starting at 2 sub, 2 sub + 2G, ... and keeps
+// four partial sums, combined in a fixed order. val and col must be 16- and 8-byte
+// aligned at index 0 (allocation alignment).
+__device__ __forceinline__ double row_dot_pairs(const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                const double* __restrict__ x, int64_t pb, int64_t pe, int sub,
+                                                int G) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if ((pb & 1) && pb < pe) {
+        if (sub == 0) a0 = val[pb] * __ldg(x + col[pb]);
+        ++pb;
+    }
+    for (int64_t p = pb + 2 * sub; p < pe; p += 4 * (int64_t)G) {
+        const int64_t q = p + 2 * (int64_t)G;
+        double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
+        int2 c0 = make_int2(-1, -1), c1 = make_int2(-1, -1);
+        if (p + 1 < pe) {
+            v0 = __ldcs(reinterpret_cast<const double2*>(val + p));
+            c0 = __ldcs(reinterpret_cast<const int2*>(col + p));
+        } else if (p < pe) {
+            v0.x = val[p];
+            c0.x = col[p];
+        }
+        if (q + 1 < pe) {
+            v1 = __ldcs(reinterpret_cast<const double2*>(val + q));
+            c1 = __ldcs(reinterpret_cast<const int2*>(col + q));
+        } else if (q < pe) {
+            v1.x = val[q];
+            c1.x = col[q];
+        }
+        if (c0.x >= 0) a0 = fma(v0.x, __ldg(x + c0.x), a0);
+        if (c0.y >= 0) a1 = fma(v0.y, __ldg(x + c0.y), a1);
+        if (c1.x >= 0) a2 = fma(v1.x, __ldg(x + c1.x), a2);
+        if (c1.y >= 0) a3 = fma(v1.y, __ldg(x + c1.y), a3);
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
 // One scalar step of LSQR after alpha_{i+1} is known (run by a single thread).
 __device__ __forceinline__ void lsqr_scalar_step(LsqrState* st, double alpha_new, double* hist) {
     const double beta = st->beta;

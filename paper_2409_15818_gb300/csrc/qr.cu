@@ -584,11 +584,13 @@ static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScrat
         void* args[] = {&A, (void*)&lda, (void*)&s, (void*)&j0, (void*)&nbw, (void*)&chunk, &tau, &Tm, &part,
                         (void*)&q.bar, &spin_ll, &err};
         cudaError_t ce;
+        const int tkp = kt_begin(kFamPanel, st);
         if (use_smem)
             ce = cudaLaunchCooperativeKernel((const void*)k_panel<T, true>, dim3(G), dim3(kPanelThreads), args, smem, st);
         else
             ce = cudaLaunchCooperativeKernel((const void*)k_panel<T, false>, dim3(G), dim3(kPanelThreads), args, 0, st);
         CSLS_CUDA(ce);
+        kt_end(tkp, 0.0, st);
         ++nl;
         const int64_t nprime = n - j0 - nbw;
         if (nprime <= 0) continue;
@@ -600,6 +602,8 @@ static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScrat
         while (ks > 1 && ks * kPanel * ntn * kVtcN > q.wp_elems * (int64_t)(8 / sizeof(T))) --ks;
         const int64_t kc = round_up(ceil_div(L, ks), kVtcRows);
         ks = ceil_div(L, kc);
+        const double prod_flop = 2.0 * (double)L * (double)nprime * (double)nbw;
+        int tk = kt_begin(kFamVtc, st);
         if (sizeof(T) == 8)
             k_vtc_f64<<<dim3((unsigned)ntn, (unsigned)ks), 256, 0, st>>>((const double*)A, lda, s, n, j0, nbw, kc,
                                                                          (double*)Wp, nprime);
@@ -607,14 +611,17 @@ static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScrat
             k_vtc_f32<<<dim3((unsigned)ntn, (unsigned)ks), 256, 0, st>>>((const float*)A, lda, s, n, j0, nbw, kc,
                                                                          (float*)Wp, nprime);
         CSLS_CUDA(cudaGetLastError());
+        kt_end(tk, prod_flop, st);
         k_wreduce<T><<<(unsigned)ceil_div(nprime, 256), 256, 0, st>>>(Wp, (int)ks, Tm, nbw, Wn, nprime);
         CSLS_CUDA(cudaGetLastError());
         dim3 ug((unsigned)ceil_div(L, kUpdM), (unsigned)ceil_div(nprime, kUpdN));
+        tk = kt_begin(kFamUpdate, st);
         if (sizeof(T) == 8)
             k_update_f64<<<ug, 256, 0, st>>>((double*)A, lda, s, n, j0, nbw, (const double*)Wn, nprime);
         else
             k_update_f32<<<dim3((unsigned)ceil_div(L, kUpdM32), ug.y), 256, 0, st>>>((float*)A, lda, s, n, j0, nbw, (const float*)Wn, nprime);
         CSLS_CUDA(cudaGetLastError());
+        kt_end(tk, prod_flop, st);
         nl += 3;
     }
     if (launches) *launches += nl;

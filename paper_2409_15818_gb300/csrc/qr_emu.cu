@@ -552,7 +552,11 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
             k_panel_top_to_f64<<<tg, 256, 0, st>>>(A, lda, j0, nbw, e.E);
             CSLS_CUDA(cudaGetLastError());
         }
-        CSLS_TRY(qr_panel_launch_f64(A, lda, s, j0, nbw, q, err, spin, st));
+        {
+            const int tk = kt_begin(kFamPanel, st);
+            CSLS_TRY(qr_panel_launch_f64(A, lda, s, j0, nbw, q, err, spin, st));
+            kt_end(tk, 0.0, st);
+        }
         nl += 3;
         const int64_t nprime = n - j0 - nbw;
         if (nprime <= 0) continue;
@@ -574,18 +578,23 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         while (ks > 1 && ks * kPanel * ntn * kVtcCols > q.wp_elems) --ks;
         const int64_t kc = round_up(ceil_div(L, ks), kVtcStep);
         ks = ceil_div(L, kc);
+        const double prod_flop = 2.0 * (double)L * (double)nprime * (double)nbw;
+        int tk = kt_begin(kFamVtc, st);
         k_emu_vtc<<<dim3((unsigned)ntn, (unsigned)ks), kEmuThreads, sizeof(VtcSmem), st>>>(
             reinterpret_cast<const long long*>(A), lda, s, n, j0, nbw, kc, e.VTd, ldvp, e.ecol, e.E, q.Wp, nprime);
         CSLS_CUDA(cudaGetLastError());
+        kt_end(tk, prod_flop, st);
         CSLS_TRY(qr_wreduce_launch_f64(q, (int)ks, nbw, nprime, st));
         // digits of Wn, then the exact update
         const int64_t ldwp = round_up(nprime, 8);
         k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 256)), 256, 0, st>>>(q.Wn, nprime, ldwp, e.Wd, e.gcol);
         CSLS_CUDA(cudaGetLastError());
+        tk = kt_begin(kFamUpdate, st);
         k_emu_update<<<dim3((unsigned)ceil_div(L, kUpdRows), (unsigned)ceil_div(nprime, kUpdCols)), kEmuThreads,
                        sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n, j0, nbw, e.Vd, ldvp,
                                               e.frow, e.Wd, ldwp, e.gcol, e.E, nprime);
         CSLS_CUDA(cudaGetLastError());
+        kt_end(tk, prod_flop, st);
         nl += 6;
     }
     if (launches) *launches += nl;

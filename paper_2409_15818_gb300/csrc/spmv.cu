@@ -13,6 +13,7 @@ __device__ __forceinline__ double group_sum(double v, int G) {
     return v;
 }
 
+
 // MODE 0: y = A x. MODE 1: ut = A z - (alpha/beta) ut, beta_{i+1} = ||ut||.
 // MODE 2: ut = b, beta_1 = ||b|| and the LSQR start values.
 template <int G, int MODE>
@@ -30,20 +31,32 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const do
     const int64_t warp_g = ((int64_t)blockIdx.x * kSpThreads + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kSpThreads) >> 5;
     double sq = 0.0;
-    for (int64_t base = warp_g * rows_per_warp; base < m; base += nwarps * rows_per_warp) {
-        const int64_t i = base + (lane / G);
+    const int64_t stride = nwarps * rows_per_warp;
+    // the next row's bounds (and old u entry) are loaded before the current row's data
+    int64_t i = warp_g * rows_per_warp + (lane / G);
+    int64_t pb = 0, pe = 0;
+    double yo = 0.0;
+    if (i < m) {
+        if (MODE != 2) { pb = rp[i]; pe = rp[i + 1]; }
+        if (MODE == 1 && sub == 0) yo = y[i];
+    }
+    for (int64_t base = warp_g * rows_per_warp; base < m; base += stride) {
         const bool active = i < m;
-        double acc = 0.0;
-        if (MODE != 2 && active) {
-            const int64_t pe = rp[i + 1];
-            for (int64_t p = rp[i] + sub; p < pe; p += G) acc += val[p] * __ldg(x + col[p]);
+        const int64_t inext = i + stride;
+        int64_t nb = 0, ne = 0;
+        double yn = 0.0;
+        if (inext < m) {
+            if (MODE != 2) { nb = rp[inext]; ne = rp[inext + 1]; }
+            if (MODE == 1 && sub == 0) yn = y[inext];
         }
+        double acc = 0.0;
+        if (MODE != 2 && active) acc = row_dot(col, val, x, pb, pe, sub, G);
         if (MODE != 2) acc = group_sum(acc, G);
         if (active && sub == 0) {
             if (MODE == 0) {
                 y[i] = acc;
             } else if (MODE == 1) {
-                const double un = acc - coef * y[i];
+                const double un = acc - coef * yo;
                 y[i] = un;
                 sq += un * un;
             } else {
@@ -52,6 +65,7 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const do
                 sq += bi * bi;
             }
         }
+        i = inext; pb = nb; pe = ne; yo = yn;
     }
     if constexpr (MODE == 0) {
         return;
@@ -97,22 +111,28 @@ k_spmv_t(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const 
     const int rows_per_warp = 32 / G;
     const int64_t warp_g = ((int64_t)blockIdx.x * kSpThreads + tid) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kSpThreads) >> 5;
-    for (int64_t base = warp_g * rows_per_warp; base < n; base += nwarps * rows_per_warp) {
-        const int64_t j = base + (lane / G);
+    const int64_t stride = nwarps * rows_per_warp;
+    int64_t j = warp_g * rows_per_warp + (lane / G);
+    int64_t pb = 0, pe = 0;
+    if (j < n) { pb = rp[j]; pe = rp[j + 1]; }
+    for (int64_t base = warp_g * rows_per_warp; base < n; base += stride) {
         const bool active = j < n;
+        const int64_t jnext = j + stride;
+        int64_t nb = 0, ne = 0;
+        if (jnext < n) { nb = rp[jnext]; ne = rp[jnext + 1]; }
         double acc = 0.0;
-        if (active) {
-            const int64_t pe = rp[j + 1];
-            for (int64_t p = rp[j] + sub; p < pe; p += G) acc += val[p] * __ldg(x + col[p]);
-        }
+        if (active) acc = G == 32 ? row_dot_pairs(col, val, x, pb, pe, sub, G) : row_dot(col, val, x, pb, pe, sub, G);
         acc = group_sum(acc, G);
         if (active && sub == 0) y[j] = acc * scale;
+        j = jnext; pb = nb; pe = ne;
     }
 }
 
+// Lanes per row from the mean row length: two half-warp rows at a time up to ~500
+// nonzeros (more rows in flight per warp), a whole warp with paired loads beyond.
 static int pick_group(int64_t nnz, int64_t rows) {
     const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
-    if (avg >= 48) return 32;
+    if (avg >= 512) return 32;
     if (avg >= 20) return 16;
     if (avg >= 8) return 8;
     return 4;

@@ -1,6 +1,8 @@
 // Scans, segmented sorts, CSR validation and the transposed copy of A.
 #include <climits>
 
+#include <vector>
+
 #include "csls_internal.cuh"
 
 namespace csls {
@@ -14,6 +16,57 @@ int device_sm_count() {
         cached = v > 0 ? v : 1;
     }
     return cached;
+}
+
+// ------------------------------------------------------------------ per-family kernel timing
+
+namespace {
+struct KtSpan {
+    cudaEvent_t a, b;
+    int fam;
+    double flop;
+};
+struct KtState {
+    bool on = false;
+    std::vector<KtSpan> spans;
+};
+thread_local KtState kt_state;
+}  // namespace
+
+void kt_install(bool on) {
+    kt_state.on = on;
+    kt_state.spans.clear();
+}
+
+int kt_begin(int fam, cudaStream_t st) {
+    if (!kt_state.on) return -1;
+    KtSpan sp{nullptr, nullptr, fam, 0.0};
+    if (cudaEventCreate(&sp.a) != cudaSuccess || cudaEventCreate(&sp.b) != cudaSuccess) return -1;
+    cudaEventRecord(sp.a, st);
+    kt_state.spans.push_back(sp);
+    return (int)kt_state.spans.size() - 1;
+}
+
+void kt_end(int token, double flop, cudaStream_t st) {
+    if (token < 0 || token >= (int)kt_state.spans.size()) return;
+    KtSpan& sp = kt_state.spans[(size_t)token];
+    sp.flop = flop;
+    cudaEventRecord(sp.b, st);
+}
+
+void kt_collect(double ms[3], int64_t launches[3], double flop[3]) {
+    for (int f = 0; f < 3; ++f) { ms[f] = 0.0; launches[f] = 0; flop[f] = 0.0; }
+    for (KtSpan& sp : kt_state.spans) {
+        float t = 0.f;
+        if (sp.a && sp.b && cudaEventElapsedTime(&t, sp.a, sp.b) == cudaSuccess && sp.fam >= 0 && sp.fam < 3) {
+            ms[sp.fam] += t;
+            launches[sp.fam] += 1;
+            flop[sp.fam] += sp.flop;
+        }
+        if (sp.a) cudaEventDestroy(sp.a);
+        if (sp.b) cudaEventDestroy(sp.b);
+    }
+    kt_install(false);
 }
 
 // ------------------------------------------------------------------ exclusive scan (one block)
