@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--prec", default="f64emu", choices=["f64", "f32", "f64emu"])
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 solve timed beside")
     ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--variant", default="qr", choices=["qr", "svd"],
+                    help="preconditioner: QR of the sketch (Algorithm 1) or truncated SVD (Algorithm 2)")
     return ap.parse_args()
 
 
@@ -293,12 +295,15 @@ def main():
     else:
         p = config_problem(args.config)
     m, n, nnz = p.m, p.n, p.nnz
-    s = 4 * n
+    s = min(4 * n, m)
     global WORKLOAD
     WORKLOAD = WORKLOADS.get(args.config, args.config)
+    if args.config.startswith("c1_"):
+        WORKLOAD = ("rank-deficient sparse stand-in with the shape, rank and density of Table C.1's %s: m=%d n=%d "
+                    "rank=%d nnz=%d, b = A x_true" % (args.config[3:], m, n, p.info["rank"], nnz))
     A = csls.Csr.from_numpy(p.row_ptr, p.col, p.val, m, n)
     b = torch.tensor(p.b[0] if p.nrhs == 1 else p.b, device="cuda")   # cfg4a: 64 right-hand sides
-    opts = dict(seed=1, prec=args.prec, tol=1e-12)
+    opts = dict(seed=1, prec=args.prec, tol=1e-12, variant=args.variant)
     stream = torch.cuda.current_stream()
 
     def step(time_kernels=0):
@@ -448,8 +453,17 @@ def main():
         pairs = 21
         ach = pairs * kern_flop[top] / top_s / 1e12
         peak = bf16_sus
+        traffic = None
+        if top == 2:
+            # DRAM bytes per average launch: the ncu capture of one k_emu_update launch (2D RFM 6x6
+            # boxes, L=25,600 x n'=3,968) read+wrote 1.697 GB for 1.637 GB of algorithmic bytes (C in
+            # int64 read and written, digit planes); traffic scales with L n', so the average launch
+            # here moves 1.0367 x its algorithmic 16 L n' bytes (sum of L n' = flops / 64)
+            traffic = 1.0367 * (kern_flop[2] / 4.0) / max(kern_n[2], 1)
         roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on a smaller "
+                                      "case, scaled per unit (profiles/emu_update_rfm6x6.md)" if traffic else None,
                     "peak_source": src + " bf16 sustained (kernel timed inside a multi-second step)",
                     "fp64_equivalent_tflops": kern_flop[top] / top_s / 1e12, "launches": kern_n[top],
                     "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
@@ -482,6 +496,7 @@ def main():
                       "f64emu": "f64 (trailing-update products from exact bf16 digit products)"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": nnz, "s": s, "tol": 1e-12,
+                       "variant": args.variant,
                        "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (dense sketch 5.2 GB, A 173 MB)"},
             "status": csls.STATUS_NAMES.get(status, status), "iterations": int(statistics.median(iters)),

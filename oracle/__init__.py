@@ -48,7 +48,7 @@ def _load():
             "orc_spmv": (None, [i64, vp, vp, vp, vp, vp]),
             "orc_spmv_trans": (None, [i64, i64, vp, vp, vp, vp, vp]),
             "orc_lsqr": (None, [i64, i64, vp, vp, vp, vp, ctypes.c_int, vp, i64, i64, dbl, dbl, i64, i64,
-                                vp, vp, vp]),
+                                vp, vp, vp, vp]),
             "orc_hhqr_solve": (None, [i64, i64, vp, i64, vp, vp, vp]),
             "orc_jacobi_svd": (ctypes.c_int, [i64, vp, i64, vp, vp, i64, ctypes.c_int]),
             "orc_svd_precond": (i64, [i64, vp, vp, i64, dbl, vp, i64]),
@@ -146,10 +146,11 @@ def spmv_trans(A, u):
     return y
 
 
-def lsqr(A, b, F, kind="qr", atol=1e-12, btol=1e-12, maxit=None, fixed_iters=0, history=False):
+def lsqr(A, b, F, kind="qr", atol=1e-12, btol=1e-12, maxit=None, fixed_iters=0, history=False, x0=None):
     """Implicit-form preconditioned LSQR: B = A R^{-1} (kind 'qr', F = R) or
-    B = A P (kind 'svd', F = P, n x r). Returns (x, info[, rnorm history])."""
+    B = A P (kind 'svd', F = P, n x r), from x0 (default 0). Returns (x, info[, rnorm history])."""
     rp, cl, vl = _csr(A)
+    x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
     F = np.asfortranarray(F, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     maxit = A.n if maxit is None else maxit
@@ -159,7 +160,8 @@ def lsqr(A, b, F, kind="qr", atol=1e-12, btol=1e-12, maxit=None, fixed_iters=0, 
     hist = np.zeros(nhist)
     r = F.shape[1]
     _load().orc_lsqr(A.m, A.n, _p(rp), _p(cl), _p(vl), _p(b), 0 if kind == "qr" else 1, _p(F), F.shape[0], r,
-                     atol, btol, maxit, fixed_iters, _p(x), _p(out), _p(hist))
+                     atol, btol, maxit, fixed_iters, _p(x0) if x0 is not None else None, _p(x), _p(out),
+                     _p(hist))
     info = dict(iterations=int(out[0]), istop=int(out[1]), rnorm=out[2], arnorm=out[3], anorm=out[4],
                 ynorm=out[5])
     if history:
@@ -238,11 +240,43 @@ def factor(A, s, seed, variant="qr", prec="f64", rcond=None):
     return dict(kind="svd", F=P, R=R, sigma=sigma, V=V, r=r, s=s, SA=SA)
 
 
+def sketch_solve(A, b, s, seed, fac=None):
+    """x0 = argmin ||S (A x - b)||: the sketch-and-solve point that Remark 3.1's y0 = Q^T (S b)
+    stands for (y0 = R x0), from LAPACK's least squares on the sketched system."""
+    h, d = hash_rows(A.m, s, seed)
+    SA = fac["SA"] if fac is not None else sketch(A, s, h, d)
+    Sb = sketch_vector(b, s, h, d)
+    return np.linalg.lstsq(SA, Sb, rcond=None)[0], Sb
+
+
+def sketch_vector(b, s, h, d):
+    """S b for a dense m-vector (Definition 2.3; rows summed in ascending order per bucket)."""
+    m = len(b)
+    one = _Csr1(m, np.arange(m + 1, dtype=np.int64), np.zeros(m, np.int32), np.ascontiguousarray(b, np.float64))
+    return sketch(one, s, h, d)[:, 0]
+
+
+class _Csr1:
+    """b as an m x 1 CSR matrix (one nonzero per row)."""
+
+    def __init__(self, m, row_ptr, col, val):
+        self.m, self.n, self.row_ptr, self.col, self.val = m, 1, row_ptr, col, val
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+
 def csqrp_lsqr(A, b, gamma=4.0, s=None, seed=1, variant="qr", prec="f64", tol=1e-12, maxit=None,
-               fixed_iters=0, history=False):
-    """Full CSQRP-LSQR (Algorithm 1) / CSSVDP-LSQR (Algorithm 2) in the implicit form."""
+               fixed_iters=0, history=False, warm=False):
+    """Full CSQRP-LSQR (Algorithm 1) / CSSVDP-LSQR (Algorithm 2) in the implicit form; with warm=True
+    LSQR starts from the sketch-and-solve point of Remark 3.1."""
     s = sketch_size(A, gamma, s)
     fac = factor(A, s, seed, variant, prec)
+    x0 = None
+    if warm:
+        x0, _ = sketch_solve(A, b, s, seed, fac)
+        fac = dict(fac, x0=x0)
     res = lsqr(A, b, fac["F"], fac["kind"], atol=tol, btol=tol, maxit=maxit, fixed_iters=fixed_iters,
-               history=history)
+               history=history, x0=x0)
     return (fac,) + tuple(res)

@@ -237,10 +237,14 @@ static double nrm2(int64_t n, const double* x) {
  * out[0..5] = iterations, istop (0 maxit/fixed, 1 S1, 2 S2, 3 exact zero
  * alpha or beta), ||r|| estimate, ||B^T r|| estimate, ||B|| estimate, ||y||.
  * rhist (may be NULL) receives ||r_k|| estimates for k = 0..iterations. */
+/* x0 (n, may be NULL): initial guess. LSQR then runs on the residual r0 = b - A x0
+ * (the preconditioned correction starts at y = 0) and returns x = x0 + M y; the
+ * stopping rule S1 keeps ||b|| of the original right-hand side, as LSQR with an
+ * initial point does (Remark 3.1 uses x0 = R^-1 Q^T S b). */
 void orc_lsqr(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
               const double* val, const double* b, int prec_kind, const double* F,
               int64_t ldf, int64_t r, double atol, double btol, int64_t maxit,
-              int64_t fixed_iters, double* x, double* out, double* rhist) {
+              int64_t fixed_iters, const double* x0, double* x, double* out, double* rhist) {
     orc_prec M = {prec_kind, n, prec_kind == 0 ? n : r, F, ldf};
     int64_t nr = M.r;
     double* u = (double*)calloc((size_t)m, sizeof(double));
@@ -251,10 +255,14 @@ void orc_lsqr(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
     double* g = (double*)calloc((size_t)n, sizeof(double));
     double* t = (double*)calloc((size_t)m, sizeof(double));
 
-    /* beta_1 u_1 = b, alpha_1 v_1 = B^T u_1 */
+    /* beta_1 u_1 = b - A x0, alpha_1 v_1 = B^T u_1 */
     memcpy(u, b, sizeof(double) * (size_t)m);
+    double bnorm = nrm2(m, u);
+    if (x0) {
+        orc_spmv(m, row_ptr, col, val, x0, t);
+        for (int64_t i = 0; i < m; ++i) u[i] -= t[i];
+    }
     double beta = nrm2(m, u);
-    double bnorm = beta;
     int64_t it = 0;
     int istop = 0;
     double alpha = 0.0, rnorm = beta, arnorm = 0.0, anorm2 = 0.0, ynorm = 0.0;
@@ -317,6 +325,8 @@ void orc_lsqr(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
         }
     }
     prec_apply(&M, y, x);
+    if (x0)
+        for (int64_t k = 0; k < n; ++k) x[k] += x0[k];
     out[0] = (double)it; out[1] = (double)istop; out[2] = rnorm; out[3] = arnorm;
     out[4] = sqrt(anorm2); out[5] = ynorm;
     free(u); free(v); free(w); free(y); free(z); free(g); free(t);

@@ -354,3 +354,76 @@ def test_adjoint_matches_finite_differences():
         fd_v.append((loss(A.val + e, b)[0] - loss(A.val - e, b)[0]) / (2 * e[p]))
     fd_v = np.array(fd_v)
     assert np.abs(gv - fd_v).max() <= 1e-5 * np.abs(fd_v).max()
+
+
+# ----------------------------------------------------------------------------- warm start (Remark 3.1)
+
+def test_lsqr_initial_guess_matches_scipy_lsqr():
+    """LSQR from an initial point x0 (M = I) against SciPy's LSQR with the same x0: iterates and the
+    converged solution (SciPy also keeps ||b|| of the original right-hand side in its stopping rule)."""
+    rng = np.random.default_rng(3)
+    A = random_sparse(300, 20, 5, rng)
+    b = rng.standard_normal(300)
+    x0 = rng.standard_normal(20)
+    As = scipy.sparse.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.m, A.n))
+    for k in range(1, 6):
+        x, _ = oracle.lsqr(A, b, np.eye(A.n), "qr", fixed_iters=k, x0=x0)
+        xs = scipy.sparse.linalg.lsqr(As, b, x0=x0, atol=0, btol=0, iter_lim=k)[0]
+        assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+    x, info = oracle.lsqr(A, b, np.eye(A.n), "qr", atol=1e-14, btol=1e-14, maxit=500, x0=x0)
+    ref = scipy.sparse.linalg.lsqr(As, b, x0=x0, atol=1e-14, btol=1e-14, iter_lim=500)
+    assert np.linalg.norm(x - ref[0]) <= 1e-12 * np.linalg.norm(ref[0])
+    assert info["iterations"] == ref[2]
+
+
+def test_sketch_vector_is_the_sketch_of_b():
+    """S b for a dense vector: a unit vector e_i lands as d(i) in bucket h(i); S is linear."""
+    m, s = 50, 12
+    h, d = oracle.hash_rows(m, s, 4)
+    for i in (0, 7, 49):
+        e = np.zeros(m)
+        e[i] = 1.0
+        want = np.zeros(s)
+        want[h[i]] = d[i]
+        assert np.array_equal(oracle.sketch_vector(e, s, h, d), want)
+    rng = np.random.default_rng(1)
+    b1, b2 = rng.integers(-5, 5, m).astype(float), rng.integers(-5, 5, m).astype(float)
+    assert np.array_equal(oracle.sketch_vector(b1 + 2 * b2, s, h, d),
+                          oracle.sketch_vector(b1, s, h, d) + 2 * oracle.sketch_vector(b2, s, h, d))
+
+
+def test_sketch_solve_point_solves_the_sketched_problem():
+    """x0 = R^-1 Q^T (S b) minimises ||S (A x - b)|| (its normal equations hold), and as a subspace
+    embedding's sketch-and-solve point it fits the data nearly as well as the true solution."""
+    rng = np.random.default_rng(8)
+    A = random_sparse(4000, 60, 6, rng)
+    Ad = A.dense()
+    xt = rng.standard_normal(60)
+    b = Ad @ xt + 0.1 * rng.standard_normal(4000)
+    s = 240
+    x0, Sb = oracle.sketch_solve(A, b, s, seed=2)
+    h, d = oracle.hash_rows(A.m, s, 2)
+    SA = oracle.sketch(A, s, h, d)
+    g = SA.T @ (SA @ x0 - Sb)
+    assert np.linalg.norm(g) <= 1e-10 * np.linalg.norm(SA) * np.linalg.norm(Sb)
+    # the same point from the Householder R of the sketch: y0 = Q^T S b, x0 = R^-1 y0
+    F, tau = oracle.householder_qr(np.column_stack([SA, Sb]))
+    R = np.triu(F[:60, :60])
+    y0 = F[:60, 60]
+    assert np.linalg.norm(np.linalg.solve(R, y0) - x0) <= 1e-10 * np.linalg.norm(x0)
+    x_star = np.linalg.lstsq(Ad, b, rcond=None)[0]
+    assert np.linalg.norm(Ad @ x0 - b) <= 2.0 * np.linalg.norm(Ad @ x_star - b)
+
+
+def test_warm_start_fewer_iterations_same_solution_cfg1():
+    """Remark 3.1's starting point cuts LSQR iterations (the paper's elasticity and Poisson tables)
+    and leaves the least-squares solution unchanged."""
+    p = config_problem("cfg1")
+    _, xc, ic = oracle.csqrp_lsqr(p, p.b[0], seed=11)
+    fac, xw, iw = oracle.csqrp_lsqr(p, p.b[0], seed=11, warm=True)
+    assert iw["iterations"] < ic["iterations"]
+    Ad = p.dense()
+    x_hh, _ = oracle.hhqr_solve(Ad, p.b[0])
+    spread = np.linalg.norm(Ad @ (x_hh - xc)) / np.linalg.norm(Ad @ xc)
+    assert np.linalg.norm(Ad @ (xw - xc)) <= max(1e-10, 2 * spread) * np.linalg.norm(Ad @ xc)
+    assert abs(np.linalg.norm(p.b[0] - Ad @ xw) - np.linalg.norm(p.b[0] - Ad @ xc)) <= 1e-12 * np.linalg.norm(p.b[0])

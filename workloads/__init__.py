@@ -7,9 +7,11 @@ path's tests and the CPU oracle's tests draw their inputs from here.
 """
 from .rng import splitmix_uniform, splitmix_normal
 from .rfm import RFMProblem, poisson2d, poisson3d
-from .synthetic import scaled_random_sparse, batched_instances, config_problem
+from .synthetic import (scaled_random_sparse, batched_instances, config_problem, rank_deficient_sparse,
+                        table_c1_problem, TABLE_C1_SHAPES)
 
 __all__ = [
     "splitmix_uniform", "splitmix_normal", "RFMProblem", "poisson2d", "poisson3d",
-    "scaled_random_sparse", "batched_instances", "config_problem",
+    "scaled_random_sparse", "batched_instances", "config_problem", "rank_deficient_sparse", "table_c1_problem",
+    "TABLE_C1_SHAPES",
 ]

@@ -69,6 +69,80 @@ def scaled_random_sparse(m, n, per_row=10, cond_exp=10.0, noise=1e-8, seed=5):
                          info=dict(seed=seed, per_row=per_row, cond_exp=cond_exp, noise=noise))
 
 
+_STREAM_RD_ROWS = 0x4D01
+_STREAM_RD_VALS = 0x4D02
+_STREAM_RD_DEPS = 0x4D03
+_STREAM_RD_PERM = 0x4D04
+
+# (m, n, rank, density) of the rank-deficient / infinite-condition matrices of the paper's Table C.1 that
+# stand in for them here (the SuiteSparse files themselves are not used); a "T" in the paper's name means
+# the transposed matrix, so m >= n throughout.
+TABLE_C1_SHAPES = {
+    "GL7d11": (1019, 60, 59, 0.024746),
+    "rel6": (2340, 157, 137, 0.013885),
+    "relat6": (2340, 157, 137, 0.022070),
+    "ch8-8-b1": (1568, 64, 63, 0.031250),
+    "shar_te2-b1": (17160, 286, 285, 0.006993),
+    "ch8-8-b2": (18816, 1568, 1505, 0.001913),
+    "rel7": (21924, 1045, 1012, 0.000024),
+    "relat7b": (21924, 1045, 1012, 0.003551),
+    "aa4T": (7195, 426, 367, 0.017005),
+    "air05T": (7195, 426, 367, 0.001700),
+    "stat96v5T": (75779, 2307, 2305, 0.001338),
+}
+
+
+def rank_deficient_sparse(m, n, rank, density, seed=7, spread_bits=16):
+    """Sparse m x n matrix of exact rank `rank` with about `density` m nonzeros per column.
+
+    Columns 0..rank-1 are independent: max(3, density m) distinct uniform rows each, small nonzero integer
+    values scaled by 2^-e with e uniform in [0, spread_bits] (a spread of the nonzero singular values; powers
+    of two keep every dependent column below an exact combination, with no rounding). Each of the other
+    n - rank columns is an integer multiple of one independent column plus another, so rank(A) = `rank` exactly
+    (checked by the callers with LAPACK). Columns are then permuted so the dependent ones are interleaved.
+    b = A x_true with x_true ~ N(0, 1): a consistent system, as in the paper's rank-deficient experiments.
+    """
+    assert 0 < rank <= n <= m
+    k = max(3, int(round(density * m)))
+    k = min(k, m)
+    cols = []
+    for j in range(rank):
+        u = splitmix_uniform(seed, _STREAM_RD_ROWS, 4 * k + 16, offset=j * (4 * k + 16))
+        rows = np.unique((u * m).astype(np.int64))[:k]
+        if rows.size < k:   # not enough distinct draws: fill deterministically
+            rows = np.unique(np.concatenate([rows, np.arange(k)]))[:k]
+        v = (splitmix_bits(seed, _STREAM_RD_VALS, rows.size, offset=j * m) % np.uint64(6)).astype(np.int64)
+        vals = np.where(v < 3, v - 3, v - 2).astype(np.float64)   # {-3, -2, -1, 1, 2, 3}
+        e = int(splitmix_bits(seed, _STREAM_RD_VALS + 1, 1, offset=j)[0] % np.uint64(spread_bits + 1))
+        c = np.zeros(m)
+        c[rows] = np.ldexp(vals, -e)
+        cols.append(c)
+    dep = splitmix_bits(seed, _STREAM_RD_DEPS, 3 * (n - rank))
+    for t in range(n - rank):
+        a = int(dep[3 * t] % np.uint64(rank))
+        b2 = int(dep[3 * t + 1] % np.uint64(rank))
+        mult = 1 + int(dep[3 * t + 2] % np.uint64(3))
+        cols.append(mult * cols[a] + (cols[b2] if b2 != a else 0.0))
+    perm = np.argsort(splitmix_uniform(seed, _STREAM_RD_PERM, n), kind="stable")
+    Ad = np.stack([cols[int(q)] for q in perm], axis=1)
+    x_true = splitmix_normal(seed, _STREAM_XTRUE, n)
+    nzr, nzc = np.nonzero(Ad)
+    order = np.lexsort((nzc, nzr))
+    nzr, nzc = nzr[order], nzc[order]
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(row_ptr, nzr + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    val = Ad[nzr, nzc]
+    b = np.bincount(nzr, weights=val * x_true[nzc], minlength=m)
+    return SparseProblem(m=m, n=n, row_ptr=row_ptr, col=nzc.astype(np.int32), val=val, b=b[None, :].copy(),
+                         x_true=x_true, info=dict(seed=seed, rank=rank, density=density))
+
+
+def table_c1_problem(name, seed=7):
+    m, n, rank, density = TABLE_C1_SHAPES[name]
+    return rank_deficient_sparse(m, n, rank, density, seed=seed)
+
+
 def batched_instances(count=32, base_seed=400, R=1.0):
     """Uneven 2D RFM instances: grid 2..6, J in {50, 100, 150}, 15..25 points per side."""
     out = []
@@ -92,6 +166,7 @@ def config_problem(name):
     cfg5_slice 1,000 x 100 with the cfg5 recipe
     rfm6x6     2D Poisson, 6x6 boxes, J=200, 30x30 points, R=2, seed 2     36,720 x 7,200 (profiling size:
                its 28,800 x 7,200 sketch is 1.7 GB, above L2 and well below HBM)
+    c1_<name>  rank-deficient stand-in with the shape, rank and density of Table C.1's <name>
     """
     if name == "cfg1":
         return poisson2d(2, 2, 100, 20, 20, R=1.0, seed=1)
@@ -108,4 +183,6 @@ def config_problem(name):
         return poisson2d(6, 6, 200, 30, 30, R=2.0, seed=2)
     if name == "cfg5_slice":
         return scaled_random_sparse(1000, 100, seed=5)
+    if name.startswith("c1_") and name[3:] in TABLE_C1_SHAPES:
+        return table_c1_problem(name[3:])
     raise KeyError(name)
