@@ -89,10 +89,15 @@ typedef struct {
     int64_t check_every;  /* host polls the convergence flag every this many iterations */
     int64_t time_kernels; /* nonzero: csls_factor brackets each launch of its three QR kernel
                              families with CUDA events and fills the kern_* report fields */
+    int64_t warm_start;   /* nonzero: csls_solve starts LSQR from the x passed in (one right-hand
+                             side): it solves for the correction from r0 = b - A x, keeps ||b|| in
+                             the stopping rule, and returns x + correction. Use with the x0 of
+                             csls_factor_warm (Remark 3.1) or any other initial guess. */
 } csls_opts;
 
 /* Defaults: gamma 4, s 0, seed 1, QR, F64, rcond 0, atol = btol = 1e-12,
- * maxit 0 (= n), fixed_iters 0, guard_cond 10, spin_limit 2e7, check_every 16, time_kernels 0. */
+ * maxit 0 (= n), fixed_iters 0, guard_cond 10, spin_limit 2e7, check_every 16, time_kernels 0,
+ * warm_start 0. */
 void csls_opts_default(csls_opts* opts);
 
 /* Host-side report, filled by csls_factor / csls_solve / csls_solve_backward. */
@@ -172,6 +177,17 @@ int csls_factor_workspace(const csls_csr* A, const csls_opts* opts, size_t* pers
 int csls_factor(const csls_csr* A, const csls_opts* opts, void* persist, size_t persist_bytes,
                 void* temp, size_t temp_bytes, csls_factor_t** factor, csls_report* rep,
                 csls_stream_t stream);
+/* csls_factor plus the warm start of Remark 3.1 (QR variant): b (m, device) is sketched with A,
+ * the QR runs on the augmented sketch [SA, Sb], whose last column then holds Q^T S b, and
+ * x0 (n, device, caller-owned) receives R^-1 (Q^T S b)(0:n) = argmin ||S (A x - b)||, the
+ * sketch-and-solve point. The factor is the same as csls_factor's; the workspace sizes are
+ * those of csls_factor_workspace (which always leaves room for the extra column). Pass x0 to
+ * csls_solve with opts->warm_start set. Errors: CSLS_ERR_ARG for the SVD variant, NULL b or
+ * x0, or s < n + 1; CSLS_ERR_NONFINITE for NaN/Inf in b. */
+int csls_factor_warm(const csls_csr* A, const double* b, const csls_opts* opts, void* persist,
+                     size_t persist_bytes, void* temp, size_t temp_bytes, csls_factor_t** factor,
+                     double* x0, csls_report* rep, csls_stream_t stream);
+
 int csls_factor_destroy(csls_factor_t* factor);
 
 /* Read-only view of a factor for inspection. *R points to the n x n upper
@@ -232,8 +248,12 @@ int csls_solve_backward(const csls_factor_t* factor, const csls_csr* A, const do
  * instance has met its stopping rule or limit (the loop condition is set on the
  * device). Each instance computes the same recurrence as csls_solve (single
  * right-hand side, QR variant). A[i], b[i] (m_i) and x[i] (n_i) are device arrays;
- * reps (host, count entries, may be NULL) is filled after a stream sync.
- * The call creates and destroys one capture stream and one graph per call. */
+ * reps (host, count entries, may be NULL) is filled after a stream sync; each
+ * report's status is that instance's, the return value the first non-OK one.
+ * Binary32 factors get the cond guard per instance (CSLS_ERR_PRECOND_GUARD), also
+ * early, after 32 and 128 iterations. opts->warm_start is not supported here
+ * (CSLS_ERR_ARG). The call creates and destroys one capture stream and one graph
+ * per call. */
 int csls_batch_solve_workspace(int64_t count, const csls_factor_t* const* factors, size_t* bytes);
 int csls_batch_solve(int64_t count, const csls_factor_t* const* factors, const csls_csr* A,
                      const double* const* b, double* const* x, const csls_opts* opts, void* work,

@@ -39,7 +39,7 @@ class csls_opts(ctypes.Structure):
                 ("variant", ctypes.c_int), ("factor_prec", ctypes.c_int), ("rcond", ctypes.c_double),
                 ("atol", ctypes.c_double), ("btol", ctypes.c_double), ("maxit", ctypes.c_int64),
                 ("fixed_iters", ctypes.c_int64), ("guard_cond", ctypes.c_double), ("spin_limit", ctypes.c_int64),
-                ("check_every", ctypes.c_int64), ("time_kernels", ctypes.c_int64)]
+                ("check_every", ctypes.c_int64), ("time_kernels", ctypes.c_int64), ("warm_start", ctypes.c_int64)]
 
 
 class csls_report(ctypes.Structure):
@@ -72,6 +72,9 @@ EXPORTS = {
     "csls_factor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
+    "csls_factor_warm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "csls_factor_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "csls_factor_view": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
     "csls_precond_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -167,7 +170,8 @@ class Csr:
 
 
 def make_opts(gamma=4.0, s=0, seed=1, variant="qr", prec="f64", rcond=0.0, atol=1e-12, btol=1e-12, maxit=0,
-              fixed_iters=0, guard_cond=10.0, spin_limit=20_000_000, check_every=16, time_kernels=0, tol=None):
+              fixed_iters=0, guard_cond=10.0, spin_limit=20_000_000, check_every=16, time_kernels=0, warm_start=0,
+              tol=None):
     o = csls_opts()
     _lib().csls_opts_default(ctypes.byref(o))
     if tol is not None:
@@ -178,6 +182,7 @@ def make_opts(gamma=4.0, s=0, seed=1, variant="qr", prec="f64", rcond=0.0, atol=
     o.maxit, o.fixed_iters = int(maxit), int(fixed_iters)
     o.guard_cond, o.spin_limit, o.check_every = float(guard_cond), int(spin_limit), int(check_every)
     o.time_kernels = int(time_kernels)
+    o.warm_start = int(warm_start)
     return o
 
 
@@ -280,6 +285,29 @@ def csls_factor(A, opts=None, stream=None, **kw):
     del temp
     _check(st, "csls_factor")
     return Factor(handle, persist, A, opts, rep.as_dict())
+
+
+def csls_factor_warm(A, b, opts=None, stream=None, **kw):
+    """csls_factor plus Remark 3.1's starting point: returns (factor, x0) with
+    x0 = argmin ||S (A x - b)|| from the QR of the augmented sketch [SA, Sb]."""
+    opts = opts or make_opts(**kw)
+    a = A.struct()
+    pb, tb = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib().csls_factor_workspace(ctypes.byref(a), ctypes.byref(opts), ctypes.byref(pb), ctypes.byref(tb)),
+           "csls_factor_workspace")
+    dev = A.val.device
+    persist = _workspace(pb.value, dev)
+    temp = _workspace(tb.value, dev)
+    b = b.contiguous()
+    x0 = torch.empty(A.n, dtype=torch.float64, device=dev)
+    handle = ctypes.c_void_p()
+    rep = csls_report()
+    st = _lib().csls_factor_warm(ctypes.byref(a), _ptr(b), ctypes.byref(opts), _ptr(persist), persist.numel(),
+                                 _ptr(temp), temp.numel(), ctypes.byref(handle), _ptr(x0), ctypes.byref(rep),
+                                 _stream(stream))
+    del temp
+    _check(st, "csls_factor_warm")
+    return Factor(handle, persist, A, opts, rep.as_dict()), x0
 
 
 def csls_precond_apply(F, v, trans=False, stream=None):

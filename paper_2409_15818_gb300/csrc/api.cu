@@ -35,6 +35,14 @@ __global__ void k_validate_csr(const int64_t* rp, const int32_t* col, const doub
     }
 }
 
+// Warm start: keep ||b|| (computed by the first start pass) for rule S1 and clear the flags that
+// pass may have set; errors stay.
+__global__ void k_keep_bnorm(csls::LsqrState* st) {
+    st->bnorm_ref = st->bnorm > 0.0 ? st->bnorm : 1e-300;
+    st->done = 0;
+    st->istop = 0;
+}
+
 __global__ void k_check_finite(const double* v, int64_t len, int* err) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
         if (!isfinite(v[i])) { set_error(err, CSLS_ERR_NONFINITE); return; }
@@ -113,16 +121,20 @@ struct FactorTemp {
     int* order;
     void* emu;
     size_t emu_bytes;
+    double* z0;          // warm start: (Q^T S b)(0:n), sign-normalised like R
+    TrsvCtl* ctl;        // warm start: x0 = R^-1 z0
+    int* flags;
 };
 
+// The sketch always has room for one more column (S b of the warm-start factorisation).
 static FactorTemp temp_carve(Carve& c, const csls_csr* A, const csls_opts* o, int64_t s) {
     FactorTemp t;
     const int64_t n = A->n;
     const int esz = o->factor_prec == CSLS_PREC_F32 ? 4 : 8;
     t.ld = round_up(s, 32);
-    t.SA = c.take<char>((size_t)(t.ld * n * esz));
+    t.SA = c.take<char>((size_t)(t.ld * (n + 1) * esz));
     t.sk = sketch_scratch_carve(c, A->m, s);
-    t.qr = qr_scratch_carve(c, s, n, esz);
+    t.qr = qr_scratch_carve(c, s, n + 1, esz);
     t.tcounts = c.take<int>((size_t)n);
     t.tcursor = c.take<int>((size_t)n);
     t.stats = c.take<double>(4);
@@ -138,9 +150,12 @@ static FactorTemp temp_carve(Carve& c, const csls_csr* A, const csls_opts* o, in
     t.emu = nullptr;
     t.emu_bytes = 0;
     if (o->factor_prec == CSLS_PREC_F64_EMU) {
-        t.emu_bytes = qr_emu_scratch_bytes(s, n);
+        t.emu_bytes = qr_emu_scratch_bytes(s, n + 1);
         t.emu = c.take<char>(t.emu_bytes);
     }
+    t.z0 = c.take<double>((size_t)n);
+    t.ctl = c.take<TrsvCtl>(1);
+    t.flags = c.take<int>((size_t)ceil_div(n, kTrsvBlock));
     return t;
 }
 
@@ -208,16 +223,31 @@ static int solve_one(const csls_factor_t* F, const csls_csr* A, const double* b,
     CSLS_CUDA(cudaMemcpyAsync(w.st, &h, sizeof(LsqrState), cudaMemcpyHostToDevice, st));
     CSLS_CUDA(cudaMemsetAsync(w.flags_up, 0, sizeof(int) * (size_t)F->nblocks, st));
     CSLS_CUDA(cudaMemsetAsync(w.flags_lo, 0, sizeof(int) * (size_t)F->nblocks, st));
-    CSLS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st));
+    const bool warm = o->warm_start != 0;
+    if (!warm) CSLS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st));
     CSLS_CUDA(cudaMemsetAsync(w.wx, 0, sizeof(double) * (size_t)n, st));
     CSLS_CUDA(cudaMemsetAsync(w.hist, 0, sizeof(double) * (size_t)(2 * (w.hist_cap + 2)), st));
     k_check_finite<<<grid_small(m), 256, 0, st>>>(b, m, &w.st->err);
     CSLS_CUDA(cudaGetLastError());
+    if (warm) {
+        k_check_finite<<<grid_small(n), 256, 0, st>>>(x, n, &w.st->err);
+        CSLS_CUDA(cudaGetLastError());
+    }
     const int spg = spmv_grid(A);
     TrsvArgs ta{F->R, F->prec, F->Dinv, n, (int)F->nblocks};
     double* hist = w.hist;
-    // start: beta_1 u_1 = b ; alpha_1 v_1 = M^T A^T u_1
-    CSLS_TRY(launch_spmv(A, 2, b, w.ut, w.st, w.sp_part, spg, st));
+    if (warm) {
+        // ||b|| for the stopping rule, then the start below runs on r0 = b - A x (the correction
+        // starts at 0 and is accumulated onto x)
+        CSLS_TRY(launch_spmv(A, 2, b, w.ut, w.st, w.sp_part, spg, st));
+        k_keep_bnorm<<<1, 1, 0, st>>>(w.st);
+        CSLS_CUDA(cudaGetLastError());
+        CSLS_TRY(launch_residual(A, x, b, w.ut, st));
+        *launches += 3;
+    }
+    const double* rhs = warm ? w.ut : b;
+    // start: beta_1 u_1 = rhs ; alpha_1 v_1 = M^T A^T u_1
+    CSLS_TRY(launch_spmv(A, 2, rhs, w.ut, w.st, w.sp_part, spg, st));
     CSLS_TRY(launch_spmv_t(F->AT, n, m, F->nnz, 1, w.ut, w.g, w.st, st));
     if (F->variant == CSLS_VARIANT_QR)
         CSLS_TRY(launch_trsv_lower(ta, 2, w.g, w.vt, nullptr, w.flags_lo, &w.st->lo, w.st, w.lo_part, hist, spin,
@@ -416,11 +446,15 @@ int csls_factor_workspace(const csls_csr* A, const csls_opts* o, size_t* persist
     return CSLS_OK;
 }
 
-int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t persist_bytes, void* temp,
-                size_t temp_bytes, csls_factor_t** factor, csls_report* rep, csls_stream_t stream) {
+// The factorisation of csls_factor; with b (warm start, QR variant only) the sketch carries S b as
+// column n, the QR runs over n + 1 columns, and x0 = R^-1 (Q^T S b)(0:n) is written to x0.
+static int factor_impl(const csls_csr* A, const double* b, double* x0, const csls_opts* o, void* persist,
+                       size_t persist_bytes, void* temp, size_t temp_bytes, csls_factor_t** factor, csls_report* rep,
+                       csls_stream_t stream) {
     if (factor) *factor = nullptr;
     CSLS_TRY(check_csr(A));
     if (!o || !factor) return CSLS_ERR_ARG;
+    if (b && (!x0 || o->variant != CSLS_VARIANT_QR || sketch_rows(A, o) < A->n + 1)) return CSLS_ERR_ARG;
     if (o->variant != CSLS_VARIANT_QR && o->variant != CSLS_VARIANT_SVD) return CSLS_ERR_ARG;
     if (o->factor_prec != CSLS_PREC_F64 && o->factor_prec != CSLS_PREC_F32 && o->factor_prec != CSLS_PREC_F64_EMU)
         return CSLS_ERR_ARG;
@@ -449,22 +483,42 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
     EventTimer t_sk(st);
     const int sk_prec = o->factor_prec == CSLS_PREC_F32 ? CSLS_PREC_F32 : CSLS_PREC_F64;
     CSLS_TRY(sketch_run(A, s, o->seed, sk_prec, ft.SA, ft.ld, ft.sk, ft.err, st, &launches));
+    const int esz = sk_prec == CSLS_PREC_F32 ? 4 : 8;
+    if (b) {
+        k_check_finite<<<grid_small(A->m), 256, 0, st>>>(b, A->m, ft.err);
+        CSLS_CUDA(cudaGetLastError());
+        CSLS_TRY(sketch_vec_run(ft.sk, b, s, o->seed, sk_prec, (char*)ft.SA + (size_t)(n * ft.ld * esz), st,
+                                &launches));
+        ++launches;
+    }
+    const int64_t ncols = b ? n + 1 : n;
     const double ms_sk = t_sk.stop();
     KtScope kts(o->time_kernels != 0);
     EventTimer t_qr(st);
     const long long spin = o->spin_limit;
     if (o->factor_prec == CSLS_PREC_F64 || o->factor_prec == CSLS_PREC_F64_EMU) {
         if (o->factor_prec == CSLS_PREC_F64)
-            CSLS_TRY(qr_factor_f64((double*)ft.SA, ft.ld, s, n, ft.qr, ft.err, spin, st, &launches));
+            CSLS_TRY(qr_factor_f64((double*)ft.SA, ft.ld, s, ncols, ft.qr, ft.err, spin, st, &launches));
         else
-            CSLS_TRY(qr_factor_f64_emu((double*)ft.SA, ft.ld, s, n, ft.qr, ft.emu, ft.emu_bytes, ft.err, spin, st,
+            CSLS_TRY(qr_factor_f64_emu((double*)ft.SA, ft.ld, s, ncols, ft.qr, ft.emu, ft.emu_bytes, ft.err, spin, st,
                                        &launches));
         CSLS_TRY(qr_extract_r_f64((const double*)ft.SA, ft.ld, n, (double*)fp.R, ft.stats, st));
         CSLS_TRY(diag_block_inverses_f64((const double*)fp.R, n, fp.Dinv, st));
+        if (b) CSLS_TRY(qr_extract_qtb_f64((const double*)ft.SA, ft.ld, n, ft.z0, st));
     } else {
-        CSLS_TRY(qr_factor_f32((float*)ft.SA, ft.ld, s, n, ft.qr, ft.err, spin, st, &launches));
+        CSLS_TRY(qr_factor_f32((float*)ft.SA, ft.ld, s, ncols, ft.qr, ft.err, spin, st, &launches));
         CSLS_TRY(qr_extract_r_f32((const float*)ft.SA, ft.ld, n, (float*)fp.R, ft.stats, st));
         CSLS_TRY(diag_block_inverses_f32((const float*)fp.R, n, fp.Dinv, st));
+        if (b) CSLS_TRY(qr_extract_qtb_f32((const float*)ft.SA, ft.ld, n, ft.z0, st));
+    }
+    if (b) {
+        // x0 = R^-1 z0: the minimiser of ||S (A x - b)|| (Remark 3.1's y0 = Q^T S b, x0 = R^-1 y0)
+        TrsvArgs ta{fp.R, o->factor_prec == CSLS_PREC_F32 ? CSLS_PREC_F32 : CSLS_PREC_F64, fp.Dinv, n,
+                    (int)ceil_div(n, kTrsvBlock)};
+        CSLS_CUDA(cudaMemsetAsync(ft.ctl, 0, sizeof(TrsvCtl), st));
+        CSLS_CUDA(cudaMemsetAsync(ft.flags, 0, sizeof(int) * (size_t)ta.nb, st));
+        CSLS_TRY(launch_trsv_upper(ta, 0, ft.z0, x0, ft.flags, ft.ctl, nullptr, nullptr, nullptr, spin, ft.err, st));
+        launches += 2;
     }
     launches += 3;
     int64_t r = n;
@@ -506,6 +560,18 @@ int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t per
     F->spmv_group_t = 0;
     *factor = F;
     return CSLS_OK;
+}
+
+int csls_factor(const csls_csr* A, const csls_opts* o, void* persist, size_t persist_bytes, void* temp,
+                size_t temp_bytes, csls_factor_t** factor, csls_report* rep, csls_stream_t stream) {
+    return factor_impl(A, nullptr, nullptr, o, persist, persist_bytes, temp, temp_bytes, factor, rep, stream);
+}
+
+int csls_factor_warm(const csls_csr* A, const double* b, const csls_opts* o, void* persist, size_t persist_bytes,
+                     void* temp, size_t temp_bytes, csls_factor_t** factor, double* x0, csls_report* rep,
+                     csls_stream_t stream) {
+    if (!b || !x0) return CSLS_ERR_ARG;
+    return factor_impl(A, b, x0, o, persist, persist_bytes, temp, temp_bytes, factor, rep, stream);
 }
 
 int csls_factor_destroy(csls_factor_t* F) {
@@ -603,8 +669,9 @@ int csls_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64
     EventTimer t(st);
     int64_t launches = 0, max_it = 0;
     int status = CSLS_OK;
-    if (nrhs > 1 && F->variant == CSLS_VARIANT_QR) {
-        // block form: independent recurrences sharing each pass over A and R
+    if (nrhs > 1 && F->variant == CSLS_VARIANT_QR && !o->warm_start) {
+        // block form: independent recurrences sharing each pass over A and R (a warm start runs the
+        // columns one by one below, each from its own x)
         for (int64_t k0 = 0; k0 < nrhs; k0 += kBlockMax) {
             const int64_t nk = std::min(kBlockMax, nrhs - k0);
             csls_report rk{};

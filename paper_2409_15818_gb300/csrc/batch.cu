@@ -441,7 +441,7 @@ extern "C" int csls_batch_solve_workspace(int64_t count, const csls_factor_t* co
 extern "C" int csls_batch_solve(int64_t count, const csls_factor_t* const* F, const csls_csr* A,
                                 const double* const* b, double* const* x, const csls_opts* o, void* work,
                                 size_t work_bytes, csls_report* reps, csls_stream_t stream) {
-    if (count <= 0 || !F || !A || !b || !x || !o) return CSLS_ERR_ARG;
+    if (count <= 0 || !F || !A || !b || !x || !o || o->warm_start) return CSLS_ERR_ARG;
     size_t need = 0;
     CSLS_TRY(csls_batch_solve_workspace(count, F, &need));
     if (!work || work_bytes < need || ((uintptr_t)work & 255)) return CSLS_ERR_WORKSPACE;

@@ -160,6 +160,9 @@ size_t sketch_scratch_bytes(int64_t m, int64_t s);
 SketchScratch sketch_scratch_carve(Carve& c, int64_t m, int64_t s);
 int sketch_run(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, int64_t ld,
                const SketchScratch& sc, int* err, cudaStream_t st, int64_t* launches);
+// S b (s entries, binary64 or binary32 by prec) from the bucket lists left by sketch_run.
+int sketch_vec_run(const SketchScratch& sc, const double* b, int64_t s, uint64_t seed, int prec, void* out,
+                   cudaStream_t st, int64_t* launches);
 
 // Transpose of A (CSR of A^T) with the permutation back to A's nonzeros.
 struct Transpose {
@@ -198,6 +201,9 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
 // min |R_jj|, max |R_jj|, count of zero or non-finite diagonal entries.
 int qr_extract_r_f64(const double* A, int64_t lda, int64_t n, double* R, double* stats, cudaStream_t st);
 int qr_extract_r_f32(const float* A, int64_t lda, int64_t n, float* R, double* stats, cudaStream_t st);
+// (Q^T S b)(0:n) from column n of a factored augmented sketch, sign-normalised like R.
+int qr_extract_qtb_f64(const double* A, int64_t lda, int64_t n, double* z, cudaStream_t st);
+int qr_extract_qtb_f32(const float* A, int64_t lda, int64_t n, double* z, cudaStream_t st);
 
 // Inverses of the kTrsvBlock diagonal blocks of R, in double (NB blocks of 64 x 64).
 int diag_block_inverses_f64(const double* R, int64_t n, double* Dinv, cudaStream_t st);

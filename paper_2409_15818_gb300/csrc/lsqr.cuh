@@ -29,6 +29,7 @@ struct LsqrState {
     double cs2, sn2, zz, xxnorm;   // ||y|| estimate (Paige-Saunders xnorm recurrence)
     double inv_beta;
     double atol, btol;
+    double bnorm_ref;          // > 0: ||b|| of the original right-hand side (warm start), kept in rule S1
     long long iter, maxit, fixed, hist_cap;
     int done, istop, first, err;
     unsigned spmv_cnt, apply_cnt;
@@ -234,6 +235,8 @@ int launch_trsv_lower(const TrsvArgs& a, int mode, double* g, double* vt, double
 int launch_spmv(const csls_csr* A, int mode, const double* x, double* y, LsqrState* st, double* partials,
                 int grid, cudaStream_t s);
 // y = A^T x * scale (scale = 1 for mode 0, st->inv_beta for mode 1).
+// y = b - A x (row-parallel), the initial residual of a warm-started solve.
+int launch_residual(const csls_csr* A, const double* x, const double* b, double* y, cudaStream_t s);
 int launch_spmv_t(const Transpose& AT, int64_t n, int64_t m, int64_t nnz, int mode, const double* x, double* y,
                   LsqrState* st, cudaStream_t s);
 int spmv_grid(const csls_csr* A);

@@ -680,6 +680,30 @@ static int extract_impl(const T* A, int64_t lda, int64_t n, T* R, double* stats,
     CSLS_CUDA(cudaGetLastError());
     return CSLS_OK;
 }
+// z(i) = sign(A_ii) A(i, n), i < n: column n of the factored augmented sketch [SA, Sb] holds
+// Q^T S b in its first n rows; the sign follows the row flips that make R's diagonal
+// non-negative.
+template <class T>
+__global__ void k_extract_qtb(const T* A, int64_t lda, int64_t n, double* z) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)A[i + n * lda];
+        z[i] = A[i + i * lda] < T(0) ? -v : v;
+    }
+}
+
+int qr_extract_qtb_f64(const double* A, int64_t lda, int64_t n, double* z, cudaStream_t st) {
+    k_extract_qtb<double><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 1024)), 256, 0, st>>>(
+        A, lda, n, z);
+    CSLS_CUDA(cudaGetLastError());
+    return CSLS_OK;
+}
+int qr_extract_qtb_f32(const float* A, int64_t lda, int64_t n, double* z, cudaStream_t st) {
+    k_extract_qtb<float><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 1024)), 256, 0, st>>>(
+        A, lda, n, z);
+    CSLS_CUDA(cudaGetLastError());
+    return CSLS_OK;
+}
+
 int qr_extract_r_f64(const double* A, int64_t lda, int64_t n, double* R, double* stats, cudaStream_t st) {
     return extract_impl<double>(A, lda, n, R, stats, st);
 }

@@ -102,6 +102,39 @@ static int grid_cap(int64_t work, int threads) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// S b for a dense m-vector b from the bucket lists of the last sketch_run (same seed and s):
+// out[k] = sum over the rows i hashed to bucket k, in ascending order, of d(i) b(i), rounded
+// to T after each addition (one thread per bucket; every bucket is written, empty ones as 0).
+template <class T>
+__global__ void __launch_bounds__(256) k_sketch_vec(const int64_t* offsets, const int32_t* list, const double* b,
+                                                    int64_t s, uint64_t seed, T* out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < s; k += (int64_t)gridDim.x * blockDim.x) {
+        T acc = T(0);
+        for (int64_t e = offsets[k]; e < offsets[k + 1]; ++e) {
+            const int64_t i = list[e];
+            uint32_t bk;
+            bool neg;
+            hash_row(seed, i, (uint32_t)s, &bk, &neg);
+            T a = (T)b[i];
+            if (neg) a = -a;
+            acc = add_rn(acc, a);
+        }
+        out[k] = acc;
+    }
+}
+
+int sketch_vec_run(const SketchScratch& sc, const double* b, int64_t s, uint64_t seed, int prec, void* out,
+                   cudaStream_t st, int64_t* launches) {
+    const int blocks = grid_cap(s, 256);
+    if (prec == CSLS_PREC_F32)
+        k_sketch_vec<float><<<blocks, 256, 0, st>>>(sc.offsets, sc.list, b, s, seed, (float*)out);
+    else
+        k_sketch_vec<double><<<blocks, 256, 0, st>>>(sc.offsets, sc.list, b, s, seed, (double*)out);
+    CSLS_CUDA(cudaGetLastError());
+    if (launches) *launches += 1;
+    return CSLS_OK;
+}
+
 int sketch_run(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, int64_t ld, const SketchScratch& sc,
                int* err, cudaStream_t st, int64_t* launches) {
     (void)err;

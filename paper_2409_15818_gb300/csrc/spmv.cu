@@ -87,7 +87,7 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const do
             st->done = 1;
         }
         if (MODE == 2) {
-            st->bnorm = beta;
+            st->bnorm = st->bnorm_ref > 0.0 ? st->bnorm_ref : beta;
             st->phibar = beta;
             st->rnorm = beta;
             if (beta == 0.0) { st->done = 1; st->istop = 3; }
@@ -130,6 +130,26 @@ k_spmv_t(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const 
 
 // Lanes per row from the mean row length: two half-warp rows at a time up to ~500
 // nonzeros (more rows in flight per warp), a whole warp with paired loads beyond.
+__global__ void __launch_bounds__(kSpThreads)
+k_residual(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const double* __restrict__ val,
+           int64_t m, const double* __restrict__ x, const double* __restrict__ b, double* y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * kSpThreads) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * kSpThreads + threadIdx.x) >> 5; i < m; i += nw) {
+        double acc = group_sum(row_dot(col, val, x, rp[i], rp[i + 1], lane, 32), 32);
+        if (lane == 0) y[i] = b[i] - acc;
+    }
+}
+
+int launch_residual(const csls_csr* A, const double* x, const double* b, double* y, cudaStream_t s) {
+    int64_t g = ceil_div(A->m * 32, kSpThreads);
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (g > cap) g = cap;
+    k_residual<<<(int)(g < 1 ? 1 : g), kSpThreads, 0, s>>>(A->row_ptr, A->col, A->val, A->m, x, b, y);
+    CSLS_CUDA(cudaGetLastError());
+    return CSLS_OK;
+}
+
 static int pick_group(int64_t nnz, int64_t rows) {
     const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
     if (avg >= 512) return 32;

@@ -41,6 +41,7 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     __shared__ double part[4][kTs];
     __shared__ double rhs[kTs];
     __shared__ double coef[4];
+    __shared__ double dsm[kTs * kTs];   // this block's diagonal inverse (32 KB)
     const int tid = threadIdx.x;
     if (MODE == 1 && *(volatile int*)&st->done) return;
     if (tid == 0) {
@@ -61,18 +62,37 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     const int64_t r0 = (int64_t)b * kTs;
     const int bs = (int)(n - r0 < kTs ? n - r0 : kTs);
     const int row = tid & (kTs - 1), q = tid >> 6;
+    // The diagonal-block inverse and each off-diagonal block of R are loaded before the flag
+    // that releases them is awaited: once block c's solution is published, only its 64 z
+    // entries are still to be fetched, so the chain from block to block carries no R traffic.
+    const double* D = Dinv + (int64_t)b * kTs * kTs;
+    for (int i = tid; i < kTs * kTs; i += kTsThreads) dsm[i] = __ldg(D + i);
+    double rv[16];
+    auto load_block = [&](int c, double (&dst)[16]) {
+        const int64_t c0 = (int64_t)c * kTs;
+        const int cs = (int)(n - c0 < kTs ? n - c0 : kTs);
+        const TR* rp = R + (r0 + row) + (c0 + q * 16) * n;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) dst[kk] = (row < bs && q * 16 + kk < cs) ? ldr(rp + (int64_t)kk * n) : 0.0;
+    };
+    if (b < nb - 1) load_block(nb - 1, rv);
     double acc = 0.0;
     for (int c = nb - 1; c > b; --c) {
         const int64_t c0 = (int64_t)c * kTs;
         const int cs = (int)(n - c0 < kTs ? n - c0 : kTs);
         if (tid == 0) wait_flag(&flags[c], want, spin, err);
         __syncthreads();
-        if (row < bs) {
-            const TR* rp = R + (r0 + row) + (c0 + q * 16) * n;
-            const double* zp = z + c0 + q * 16;
+        double zv[16];
+        const double* zp = z + c0 + q * 16;
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk)
-                if (q * 16 + kk < cs) acc += ldr(rp + (int64_t)kk * n) * __ldcg(zp + kk);
+        for (int kk = 0; kk < 16; ++kk) zv[kk] = q * 16 + kk < cs ? __ldcg(zp + kk) : 0.0;
+        double rn[16];
+        if (c - 1 > b) load_block(c - 1, rn);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = fma(rv[kk], zv[kk], acc);
+        if (c - 1 > b) {
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) rv[kk] = rn[kk];
         }
     }
     part[q][row] = acc;
@@ -83,12 +103,11 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
         rhs[tid] = r;
     }
     __syncthreads();
-    const double* D = Dinv + (int64_t)b * kTs * kTs;
     double a2 = 0.0;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
         const int k = q * 16 + kk;
-        a2 += D[row + k * kTs] * rhs[k];
+        a2 += dsm[row + k * kTs] * rhs[k];
     }
     part[q][row] = a2;
     __syncthreads();
@@ -127,6 +146,7 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     __shared__ double rhs[kTs];
     __shared__ double coef[2];
     __shared__ double red[kTsThreads / 32];
+    __shared__ double dsm[kTs * kTs];   // this block's diagonal inverse (32 KB)
     const int tid = threadIdx.x;
     if (MODE == 1 && *(volatile int*)&st->done) return;
     if (tid == 0) {
@@ -140,16 +160,34 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     const int64_t r0 = (int64_t)b * kTs;
     const int bs = (int)(n - r0 < kTs ? n - r0 : kTs);
     const int col = tid & (kTs - 1), q = tid >> 6;
+    // as in the upper solve: the diagonal inverse and the next block of R are loaded ahead of
+    // the flag that releases them
+    const double* D = Dinv + (int64_t)b * kTs * kTs;
+    for (int i = tid; i < kTs * kTs; i += kTsThreads) dsm[i] = __ldg(D + i);
+    double rv[16];
+    auto load_block = [&](int c, double (&dst)[16]) {
+        const int64_t c0 = (int64_t)c * kTs;
+        const TR* rp = R + (c0 + q * 16) + (r0 + col) * n;   // column r0+col, rows c0+q*16..+16
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) dst[kk] = col < bs ? ldr(rp + kk) : 0.0;
+    };
+    if (b > 0) load_block(0, rv);
     double acc = 0.0;
     for (int c = 0; c < b; ++c) {
         const int64_t c0 = (int64_t)c * kTs;
         if (tid == 0) wait_flag(&flags[c], want, spin, err);
         __syncthreads();
-        if (col < bs) {
-            const TR* rp = R + (c0 + q * 16) + (r0 + col) * n;   // column r0+col, rows c0+q*16..+16
-            const double* zp = g + c0 + q * 16;
+        double zv[16];
+        const double* zp = g + c0 + q * 16;
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) acc += ldr(rp + kk) * __ldcg(zp + kk);
+        for (int kk = 0; kk < 16; ++kk) zv[kk] = __ldcg(zp + kk);
+        double rn[16];
+        if (c + 1 < b) load_block(c + 1, rn);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = fma(rv[kk], zv[kk], acc);
+        if (c + 1 < b) {
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) rv[kk] = rn[kk];
         }
     }
     part[q][col] = acc;
@@ -160,12 +198,11 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
         rhs[tid] = r;
     }
     __syncthreads();
-    const double* D = Dinv + (int64_t)b * kTs * kTs;
     double a2 = 0.0;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
         const int k = q * 16 + kk;
-        a2 += D[k + col * kTs] * rhs[k];   // (D^T rhs)_col
+        a2 += dsm[k + col * kTs] * rhs[k];   // (D^T rhs)_col
     }
     part[q][col] = a2;
     __syncthreads();

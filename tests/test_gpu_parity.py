@@ -418,3 +418,71 @@ def test_batch_solve_uneven_instances(csls, tmp_path):
             _, xo, _ = oracle.csqrp_lsqr(p, p.b[0], s=min(4 * p.n, p.m), seed=2 + k)
             x_hh, _ = oracle.hhqr_solve(Ad, p.b[0])
             assert _anorm_rel(Ad, xb, xo) <= max(1e-10, 2 * _anorm_rel(Ad, x_hh, xo))
+
+
+# ----------------------------------------------------------------------------- warm start (Remark 3.1)
+
+@pytest.mark.parametrize("prec", ["f64", "f64emu"])
+def test_warm_start_point_and_solve_match_oracle(csls, prec):
+    p = SKETCH_CASES["cfg1"]()
+    A = dev(csls, p)
+    b = torch.tensor(p.b[0], device="cuda")
+    s = min(4 * p.n, p.m)
+    F, x0 = csls.csls_factor_warm(A, b, seed=11, prec=prec)
+    # x0 = argmin ||S (A x - b)||: compared in the sketched norm, the one the sketched problem fixes
+    x0o, Sb = oracle.sketch_solve(p, p.b[0], s, seed=11)
+    h, d = oracle.hash_rows(p.m, s, 11)
+    SA = oracle.sketch(p, s, h, d)
+    x0g = x0.cpu().numpy()
+    assert np.linalg.norm(SA @ (x0g - x0o)) <= 1e-10 * np.linalg.norm(SA @ x0o)
+    # LSQR from x0: same solution as the cold start and the oracle's warm run, in fewer iterations
+    xw, repw = csls.csls_solve(F, A, b, x=x0.clone(), warm_start=1)
+    xc, repc = csls.csls_solve(F, A, b)
+    _, xo, io = oracle.csqrp_lsqr(p, p.b[0], seed=11, warm=True)
+    _, xoc, _ = oracle.csqrp_lsqr(p, p.b[0], seed=11)
+    Ad = p.dense()
+    x_hh, _ = oracle.hhqr_solve(Ad, p.b[0])
+    # reading R2: solutions that meet the 1e-12 stopping rule lie within the O1-O2 spread of each
+    # other; the warm oracle run may land much closer to O1 than the cold one, so the spread is
+    # taken over both oracle runs
+    spread = max(_anorm_rel(Ad, x_hh, xo), _anorm_rel(Ad, x_hh, xoc))
+    assert _anorm_rel(Ad, xw.cpu().numpy(), xo) <= max(1e-10, 2 * spread)
+    assert _anorm_rel(Ad, xw.cpu().numpy(), xc.cpu().numpy()) <= max(1e-10, 2 * spread)
+    assert repw["iterations"] < repc["iterations"]
+    assert abs(repw["iterations"] - io["iterations"]) <= 3
+    assert abs(repw["bnorm"] - np.linalg.norm(p.b[0])) <= 1e-12 * np.linalg.norm(p.b[0])
+    assert repw["istop"] in (1, 2) and repw["cond_est"] < 10
+
+
+def test_warm_start_well_conditioned_exact_parity(csls):
+    rng = np.random.default_rng(31)
+    Acpu = random_sparse(3000, 120, 8, rng)
+    b = rng.standard_normal(3000)
+    A = dev(csls, Acpu)
+    F, x0 = csls.csls_factor_warm(A, torch.tensor(b, device="cuda"), s=480, seed=4)
+    x0o, _ = oracle.sketch_solve(Acpu, b, 480, seed=4)
+    assert _rel(x0.cpu().numpy(), x0o) < 1e-11
+    fac = oracle.factor(Acpu, 480, 4)
+    for k in (1, 3, 6):
+        xk, _ = csls.csls_solve(F, A, torch.tensor(b, device="cuda"), x=x0.clone(), warm_start=1, fixed_iters=k)
+        xo, _ = oracle.lsqr(Acpu, b, fac["R"], "qr", fixed_iters=k, x0=x0o)
+        assert _rel(xk.cpu().numpy(), xo) < 1e-10
+    # several right-hand sides, each from its own starting point, equal the one-by-one solves
+    B = torch.tensor(np.stack([b, 2 * b + 1]), device="cuda")
+    X0 = torch.stack([x0, 2 * x0])
+    X, _ = csls.csls_solve(F, A, B, x=X0.clone(), warm_start=1)
+    for k in range(2):
+        xk, _ = csls.csls_solve(F, A, B[k], x=X0[k].clone(), warm_start=1)
+        assert torch.equal(X[k], xk)
+
+
+def test_warm_start_argument_errors(csls):
+    p = SKETCH_CASES["cfg1"]()
+    A = dev(csls, p)
+    b = torch.tensor(p.b[0], device="cuda")
+    with pytest.raises(csls.CslsError) as e:
+        csls.csls_factor_warm(A, b, seed=1, variant="svd")
+    assert e.value.status == 1
+    F = csls.csls_factor(A, seed=1)
+    _, _, st = csls.csls_batch_solve([F], [A], [b], warm_start=1, raise_on_error=False)
+    assert st == 1
