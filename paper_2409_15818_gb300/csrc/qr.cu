@@ -81,11 +81,17 @@ k_panel(T* A, int64_t lda, int64_t s, int64_t j0, int nbw, int64_t chunk, T* tau
             if (j >= r0 && j < r1) part_alpha[0] = W[c * ld + (j - r0)];
         }
         if (!grid_sync(bar, G, spin, err)) return;
-        // (b) reflector: every CTA reduces the partials in the same order
+        // (b) reflector: every CTA reduces the partials in the same fixed tree order (all threads
+        // load, so the G partials cost one round trip instead of G dependent ones)
+        T sq = T(0);
+        for (int q = tid; q < G; q += kPanelThreads) sq += __ldcg(part_norm + q);
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if ((tid & 31) == 0) red[tid >> 5] = sq;
+        __syncthreads();
         if (tid == 0) {
             T sigma = T(0);
-            for (int q = 0; q < G; ++q) sigma += part_norm[q];
-            T alpha = part_alpha[0];
+            for (int w = 0; w < kPanelThreads / 32; ++w) sigma += red[w];
+            T alpha = __ldcg(part_alpha);
             if (sigma == T(0)) {
                 coef[0] = T(0); coef[1] = T(1); coef[2] = alpha; coef[3] = T(0);
             } else {
@@ -125,11 +131,16 @@ k_panel(T* A, int64_t lda, int64_t s, int64_t j0, int nbw, int64_t chunk, T* tau
             if (lane == 0) part_w[(int64_t)g * kPanel + k] = a2;
         }
         if (!grid_sync(bar, G, spin, err)) return;
-        // (d) w_k = tau sum_g partials; A(j:s, k) -= w_k v
-        if (tid < nbw && tid > c) {
+        // (d) w_k = tau sum_g partials (8 threads per column, fixed order); A(j:s, k) -= w_k v
+        {
+            const int k = tid >> 3, sub = tid & 7;
             T t = T(0);
-            for (int q = 0; q < G; ++q) t += part_w[(int64_t)q * kPanel + tid];
-            wk[tid] = tau_c * t;
+            if (k < nbw && k > c)
+                for (int q = sub; q < G; q += 8) t += __ldcg(part_w + (int64_t)q * kPanel + k);
+            t += __shfl_xor_sync(0xffffffffu, t, 4);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            if (sub == 0 && k < nbw && k > c) wk[k] = tau_c * t;
         }
         __syncthreads();
         const int ncols = nbw - c - 1;
