@@ -192,6 +192,10 @@ int qr_factor_f64(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch&
                   long long spin_limit, cudaStream_t st, int64_t* launches);
 int qr_factor_f32(float* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, int* err,
                   long long spin_limit, cudaStream_t st, int64_t* launches);
+// The FP64 (DMMA) update of columns [j0 + nbw, n_end) by the panel at j0 whose T is in q.T
+// (used inside the emulated path's outer blocks; not timed by the kernel timer).
+int qr_trailing_update_f64(double* A, int64_t lda, int64_t s, int64_t n_end, int64_t j0, int nbw, const QrScratch& q,
+                           cudaStream_t st);
 // The same factorisation with the trailing-update products emulated exactly on the bf16
 // tensor cores (digit splitting, int64 fixed-point trailing matrix); needs emu scratch.
 size_t qr_emu_scratch_bytes(int64_t s, int64_t n);

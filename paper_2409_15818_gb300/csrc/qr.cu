@@ -438,28 +438,32 @@ __global__ void __launch_bounds__(256) k_vtc_f32(const float* A, int64_t lda, in
     }
 }
 
-// Wn(a, c) = -sum_{b <= a} T(b, a) sum_ks Wp[ks](b, c)
+// Wn(a, c) = -sum_{b <= a} T(b, a) sum_ks Wp[ks](b, c). A CTA owns 32 columns: one thread per
+// (b, c) entry sums its partials (coalesced along c), then one per (a, c) forms -T^T W.
+constexpr int kWrCols = 32;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_wreduce(const T* Wp, int KS, const T* Tmat, int nbw, T* Wn, int64_t nprime) {
     __shared__ T Ts[kPanel * kPanel];
+    __shared__ T Ws[kPanel * kWrCols];
+    const int64_t c0 = (int64_t)blockIdx.x * kWrCols;
     for (int p = threadIdx.x; p < kPanel * kPanel; p += blockDim.x) Ts[p] = Tmat[p];
+    for (int i = threadIdx.x; i < kPanel * kWrCols; i += blockDim.x) {
+        const int bb = i / kWrCols, cl = i % kWrCols;
+        const int64_t c = c0 + cl;
+        T t = T(0);
+        if (bb < nbw && c < nprime)
+            for (int q = 0; q < KS; ++q) t += Wp[((int64_t)q * kPanel + bb) * nprime + c];
+        Ws[i] = t;
+    }
     __syncthreads();
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nprime; c += (int64_t)gridDim.x * blockDim.x) {
-        T w[kPanel];
-#pragma unroll
-        for (int b = 0; b < kPanel; ++b) {
-            T t = T(0);
-            if (b < nbw)
-                for (int q = 0; q < KS; ++q) t += Wp[((int64_t)q * kPanel + b) * nprime + c];
-            w[b] = t;
-        }
-#pragma unroll
-        for (int a = 0; a < kPanel; ++a) {
-            T t = T(0);
-#pragma unroll
-            for (int b = 0; b <= a; ++b) t += Ts[b + a * kPanel] * w[b];
-            Wn[(int64_t)a * nprime + c] = a < nbw ? -t : T(0);
-        }
+    for (int i = threadIdx.x; i < kPanel * kWrCols; i += blockDim.x) {
+        const int a = i / kWrCols, cl = i % kWrCols;
+        const int64_t c = c0 + cl;
+        if (c >= nprime) continue;
+        T t = T(0);
+        for (int bb = 0; bb <= a; ++bb) t += Ts[bb + a * kPanel] * Ws[bb * kWrCols + cl];
+        Wn[(int64_t)a * nprime + c] = a < nbw ? -t : T(0);
     }
 }
 
@@ -566,6 +570,49 @@ QrScratch qr_scratch_carve(Carve& c, int64_t s, int64_t n, int elem_bytes) {
     return q;
 }
 
+// Apply the panel at columns [j0, j0 + nbw) (V below its diagonal, T in Tm) to columns
+// [j0 + nbw, n): W = V^T C (split over row chunks), Wn = -T^T W, C += V Wn.
+template <class T>
+static int trailing_update(T* A, int64_t lda, int64_t s, int64_t n, int64_t j0, int nbw, const QrScratch& q,
+                           const T* Tm, cudaStream_t st, bool timed = true) {
+    const int64_t L = s - j0;
+    const int64_t nprime = n - j0 - nbw;
+    if (nprime <= 0) return CSLS_OK;
+    T* Wp = reinterpret_cast<T*>(q.Wp);
+    T* Wn = reinterpret_cast<T*>(q.Wn);
+    const int64_t ntn = ceil_div(nprime, kVtcN);
+    int64_t ks = ceil_div(4LL * device_sm_count(), ntn);
+    const int64_t maxks = ceil_div(L, kVtcRows);
+    if (ks > maxks) ks = maxks;
+    if (ks > 64) ks = 64;   // narrow trailing blocks: a few long row chunks keep the partial sums short
+    if (ks < 1) ks = 1;
+    while (ks > 1 && ks * kPanel * ntn * kVtcN > q.wp_elems * (int64_t)(8 / sizeof(T))) --ks;
+    const int64_t kc = round_up(ceil_div(L, ks), kVtcRows);
+    ks = ceil_div(L, kc);
+    const double prod_flop = 2.0 * (double)L * (double)nprime * (double)nbw;
+    int tk = timed ? kt_begin(kFamVtc, st) : -1;
+    if (sizeof(T) == 8)
+        k_vtc_f64<<<dim3((unsigned)ntn, (unsigned)ks), 256, 0, st>>>((const double*)A, lda, s, n, j0, nbw, kc,
+                                                                     (double*)Wp, nprime);
+    else
+        k_vtc_f32<<<dim3((unsigned)ntn, (unsigned)ks), 256, 0, st>>>((const float*)A, lda, s, n, j0, nbw, kc,
+                                                                     (float*)Wp, nprime);
+    CSLS_CUDA(cudaGetLastError());
+    kt_end(tk, prod_flop, st);
+    k_wreduce<T><<<(unsigned)ceil_div(nprime, kWrCols), 256, 0, st>>>(Wp, (int)ks, Tm, nbw, Wn, nprime);
+    CSLS_CUDA(cudaGetLastError());
+    dim3 ug((unsigned)ceil_div(L, kUpdM), (unsigned)ceil_div(nprime, kUpdN));
+    tk = timed ? kt_begin(kFamUpdate, st) : -1;
+    if (sizeof(T) == 8)
+        k_update_f64<<<ug, 256, 0, st>>>((double*)A, lda, s, n, j0, nbw, (const double*)Wn, nprime);
+    else
+        k_update_f32<<<dim3((unsigned)ceil_div(L, kUpdM32), ug.y), 256, 0, st>>>((float*)A, lda, s, n, j0, nbw,
+                                                                                (const float*)Wn, nprime);
+    CSLS_CUDA(cudaGetLastError());
+    kt_end(tk, prod_flop, st);
+    return CSLS_OK;
+}
+
 template <class T>
 static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, int* err, long long spin,
                           cudaStream_t st, int64_t* launches) {
@@ -574,8 +621,6 @@ static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScrat
     T* tau = reinterpret_cast<T*>(q.tau);
     T* Tm = reinterpret_cast<T*>(q.T);
     T* part = reinterpret_cast<T*>(q.partials);
-    T* Wp = reinterpret_cast<T*>(q.Wp);
-    T* Wn = reinterpret_cast<T*>(q.Wn);
     static bool attr_set[2] = {false, false};
     const int which = sizeof(T) == 8 ? 0 : 1;
     const size_t smem_cap = 200 * 1024;
@@ -603,40 +648,17 @@ static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScrat
         CSLS_CUDA(ce);
         kt_end(tkp, 0.0, st);
         ++nl;
-        const int64_t nprime = n - j0 - nbw;
-        if (nprime <= 0) continue;
-        const int64_t ntn = ceil_div(nprime, kVtcN);
-        int64_t ks = ceil_div(4LL * device_sm_count(), ntn);
-        const int64_t maxks = ceil_div(L, kVtcRows);
-        if (ks > maxks) ks = maxks;
-        if (ks < 1) ks = 1;
-        while (ks > 1 && ks * kPanel * ntn * kVtcN > q.wp_elems * (int64_t)(8 / sizeof(T))) --ks;
-        const int64_t kc = round_up(ceil_div(L, ks), kVtcRows);
-        ks = ceil_div(L, kc);
-        const double prod_flop = 2.0 * (double)L * (double)nprime * (double)nbw;
-        int tk = kt_begin(kFamVtc, st);
-        if (sizeof(T) == 8)
-            k_vtc_f64<<<dim3((unsigned)ntn, (unsigned)ks), 256, 0, st>>>((const double*)A, lda, s, n, j0, nbw, kc,
-                                                                         (double*)Wp, nprime);
-        else
-            k_vtc_f32<<<dim3((unsigned)ntn, (unsigned)ks), 256, 0, st>>>((const float*)A, lda, s, n, j0, nbw, kc,
-                                                                         (float*)Wp, nprime);
-        CSLS_CUDA(cudaGetLastError());
-        kt_end(tk, prod_flop, st);
-        k_wreduce<T><<<(unsigned)ceil_div(nprime, 256), 256, 0, st>>>(Wp, (int)ks, Tm, nbw, Wn, nprime);
-        CSLS_CUDA(cudaGetLastError());
-        dim3 ug((unsigned)ceil_div(L, kUpdM), (unsigned)ceil_div(nprime, kUpdN));
-        tk = kt_begin(kFamUpdate, st);
-        if (sizeof(T) == 8)
-            k_update_f64<<<ug, 256, 0, st>>>((double*)A, lda, s, n, j0, nbw, (const double*)Wn, nprime);
-        else
-            k_update_f32<<<dim3((unsigned)ceil_div(L, kUpdM32), ug.y), 256, 0, st>>>((float*)A, lda, s, n, j0, nbw, (const float*)Wn, nprime);
-        CSLS_CUDA(cudaGetLastError());
-        kt_end(tk, prod_flop, st);
+        if (n - j0 - nbw <= 0) continue;
+        CSLS_TRY(trailing_update<T>(A, lda, s, n, j0, nbw, q, Tm, st));
         nl += 3;
     }
     if (launches) *launches += nl;
     return CSLS_OK;
+}
+
+int qr_trailing_update_f64(double* A, int64_t lda, int64_t s, int64_t n_end, int64_t j0, int nbw, const QrScratch& q,
+                           cudaStream_t st) {
+    return trailing_update<double>(A, lda, s, n_end, j0, nbw, q, q.T, st, false);
 }
 
 int qr_panel_launch_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, const QrScratch& q, int* err,
@@ -668,7 +690,7 @@ int qr_panel_launch_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, 
 }
 
 int qr_wreduce_launch_f64(const QrScratch& q, int ks, int nbw, int64_t nprime, cudaStream_t st) {
-    k_wreduce<double><<<(unsigned)ceil_div(nprime, 256), 256, 0, st>>>(q.Wp, ks, q.T, nbw, q.Wn, nprime);
+    k_wreduce<double><<<(unsigned)ceil_div(nprime, kWrCols), 256, 0, st>>>(q.Wp, ks, q.T, nbw, q.Wn, nprime);
     CSLS_CUDA(cudaGetLastError());
     return CSLS_OK;
 }

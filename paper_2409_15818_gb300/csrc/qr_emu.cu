@@ -156,117 +156,234 @@ __global__ void k_panel_top_to_f64(double* A, int64_t lda, int64_t j0, int nbw, 
         A[r + c * lda] = E[c] > -1000 ? ldexp((double)colf[r], sh) : 0.0;
 }
 
-// ------------------------------------------------------------------ per-panel digit kernels
+// ------------------------------------------------------------------ outer-block digit kernels
+//
+// The emulated products act on outer blocks of kOB = 64 columns: two 32-wide panels are
+// factored in binary64 (the second after the first one's update, on the FP64 MMA pipe),
+// their compact-WY factors are merged, and the trailing matrix is updated once per 64
+// columns. A product with K = 64 keeps every level sum below 6 x 64 x 2^14 < 2^24, so it
+// is exact in FP32 and is read back with one rounding conversion per level.
 
-// Masked Householder vector entry: 0 above the diagonal, 1 on it, stored tail below.
-__device__ __forceinline__ double vmask(const double* A, int64_t lda, int64_t r, int64_t j0, int a) {
-    const int64_t d = j0 + a;
+constexpr int kOB = 2 * kPanel;   // 64
+
+// Masked Householder vector entry of the outer block starting at J0: 0 above the diagonal,
+// 1 on it, the stored tail below.
+__device__ __forceinline__ double vmask(const double* A, int64_t lda, int64_t r, int64_t J0, int a) {
+    const int64_t d = J0 + a;
     return r < d ? 0.0 : (r == d ? 1.0 : A[r + d * lda]);
 }
 
 // Column maxima of V (for the V^T C digits), as ordered bit patterns (|x| >= 0).
-__global__ void __launch_bounds__(256) k_vcolmax(const double* A, int64_t lda, int64_t s, int64_t j0, int nbw,
+__global__ void __launch_bounds__(256) k_vcolmax(const double* A, int64_t lda, int64_t s, int64_t J0, int nbo,
                                                  unsigned long long* colmax) {
-    __shared__ unsigned long long red[kPanel];
-    if (threadIdx.x < kPanel) red[threadIdx.x] = 0ULL;
+    __shared__ unsigned long long red[kOB];
+    if (threadIdx.x < kOB) red[threadIdx.x] = 0ULL;
     __syncthreads();
-    const int a = threadIdx.x & 31;
+    const int a = threadIdx.x & (kOB - 1);
     unsigned long long best = 0ULL;
-    if (a < nbw) {
-        for (int64_t r = j0 + blockIdx.x * 8 + (threadIdx.x >> 5); r < s; r += (int64_t)gridDim.x * 8) {
-            const unsigned long long b = __double_as_longlong(fabs(vmask(A, lda, r, j0, a)));
+    if (a < nbo) {
+        for (int64_t r = J0 + blockIdx.x * 4 + (threadIdx.x >> 6); r < s; r += (int64_t)gridDim.x * 4) {
+            const unsigned long long b = __double_as_longlong(fabs(vmask(A, lda, r, J0, a)));
             best = b > best ? b : best;
         }
         atomicMax(&red[a], best);
     }
     __syncthreads();
-    if (threadIdx.x < nbw) atomicMax(&colmax[threadIdx.x], red[threadIdx.x]);
+    if (threadIdx.x < nbo) atomicMax(&colmax[threadIdx.x], red[threadIdx.x]);
 }
 
 // Digits of V: per-row scale for C += V Wn (Vd[p][r][a], a contiguous) and per-column
-// scale for V^T C (VTd[p][a][r], r contiguous). Rows are local row indices r - j0.
-__global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, int64_t s, int64_t j0, int nbw,
+// scale for V^T C (VTd[p][a][r], r contiguous). Rows are local row indices r - J0; columns
+// a >= nbo and rows past the block are zero digits.
+__global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, int64_t s, int64_t J0, int nbo,
                                                  const unsigned long long* colmax, int64_t ldv,
                                                  unsigned short* Vd, unsigned short* VTd, int* frow, int* ecol) {
-    const int64_t L = s - j0;
-    if (blockIdx.x == 0 && threadIdx.x < kPanel)
-        ecol[threadIdx.x] = threadIdx.x < nbw ? exp_of(__longlong_as_double((long long)colmax[threadIdx.x])) : 0;
+    __shared__ int ecol_s[kOB];
+    if (threadIdx.x < kOB) {
+        const int e = threadIdx.x < nbo ? exp_of(__longlong_as_double((long long)colmax[threadIdx.x])) : 0;
+        ecol_s[threadIdx.x] = e;
+        if (blockIdx.x == 0) ecol[threadIdx.x] = e;
+    }
+    __syncthreads();
+    const int64_t L = s - J0;
     for (int64_t lr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lr < ldv; lr += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = j0 + lr;
-        double v[kPanel];
+        const int64_t r = J0 + lr;
         double mx = 0.0;
-#pragma unroll
-        for (int a = 0; a < kPanel; ++a) {
-            v[a] = (lr < L && a < nbw) ? vmask(A, lda, r, j0, a) : 0.0;
-            mx = fmax(mx, fabs(v[a]));
-        }
+        for (int a = 0; a < nbo; ++a)
+            if (lr < L) mx = fmax(mx, fabs(vmask(A, lda, r, J0, a)));
         const int f = exp_of(mx);
         frow[lr] = f;
-#pragma unroll
-        for (int a = 0; a < kPanel; ++a) {
-            int d[kDig];
-            digits_f64(v[a], f, d);
-            const int ea = a < nbw ? exp_of(__longlong_as_double((long long)colmax[a])) : 0;
-            int dt[kDig];
-            digits_f64(v[a], ea, dt);
+        for (int a = 0; a < kOB; ++a) {
+            const double v = (lr < L && a < nbo) ? vmask(A, lda, r, J0, a) : 0.0;
+            int d[kDig], dt[kDig];
+            digits_f64(v, f, d);
+            digits_f64(v, ecol_s[a], dt);
 #pragma unroll
             for (int p = 0; p < kDig; ++p) {
-                Vd[((int64_t)p * ldv + lr) * kPanel + a] = bf16_of_int(d[p]);
-                VTd[((int64_t)p * kPanel + a) * ldv + lr] = bf16_of_int(dt[p]);
+                Vd[((int64_t)p * ldv + lr) * kOB + a] = bf16_of_int(d[p]);
+                VTd[((int64_t)p * kOB + a) * ldv + lr] = bf16_of_int(dt[p]);
             }
         }
     }
 }
 
-// Digits of Wn (kPanel x nprime, row-major): per-column scale; Wd[p][c][a].
-__global__ void k_wdigits(const double* Wn, int64_t nprime, int64_t ldw, unsigned short* Wd, int* gcol) {
+// Wn = -T^T (sum of the split-K partials of W = V^T C) for the outer block (T: nbo x nbo upper
+// triangular, column-major with ld kOB); Wp[k] and Wn are kOB x nprime row-major. A CTA owns 64
+// columns: it sums their partials (coalesced along the columns) into shared memory, then each
+// thread forms entries of -T^T W from the shared copies of T and W.
+constexpr int kWrCols = 64;
+constexpr size_t kWrSmem = sizeof(double) * (kOB * kOB + kOB * kWrCols);
+
+__global__ void __launch_bounds__(256) k_wreduce_ob(const double* Wp, int ks, const double* Tb, int nbo, double* Wn,
+                                                    int64_t nprime) {
+    extern __shared__ __align__(16) unsigned char wr_raw[];
+    double* Ts = reinterpret_cast<double*>(wr_raw);   // [b + a kOB]
+    double* Ws = Ts + kOB * kOB;                      // [b][cl]
+    const int64_t c0 = (int64_t)blockIdx.x * kWrCols;
+    for (int i = threadIdx.x; i < kOB * kOB; i += blockDim.x) Ts[i] = Tb[i];
+    for (int i = threadIdx.x; i < kOB * kWrCols; i += blockDim.x) {
+        const int b = i / kWrCols, cl = i % kWrCols;
+        const int64_t c = c0 + cl;
+        double t = 0.0;
+        if (b < nbo && c < nprime)
+            for (int k = 0; k < ks; ++k) t += Wp[((int64_t)k * kOB + b) * nprime + c];
+        Ws[i] = t;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOB * kWrCols; i += blockDim.x) {
+        const int a = i / kWrCols, cl = i % kWrCols;
+        const int64_t c = c0 + cl;
+        if (a >= nbo || c >= nprime) continue;
+        double t = 0.0;
+        for (int b = 0; b <= a; ++b) t += Ts[b + a * kOB] * Ws[b * kWrCols + cl];
+        Wn[(int64_t)a * nprime + c] = -t;
+    }
+}
+
+// Digits of Wn (kOB x nprime, row-major): per-column scale; Wd[p][c][a].
+__global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw, unsigned short* Wd, int* gcol) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ldw; c += (int64_t)gridDim.x * blockDim.x) {
-        double w[kPanel];
         double mx = 0.0;
-#pragma unroll
-        for (int a = 0; a < kPanel; ++a) {
-            w[a] = c < nprime ? Wn[(int64_t)a * nprime + c] : 0.0;
-            mx = fmax(mx, fabs(w[a]));
-        }
+        for (int a = 0; a < nbo; ++a)
+            if (c < nprime) mx = fmax(mx, fabs(Wn[(int64_t)a * nprime + c]));
         const int g = exp_of(mx);
         gcol[c] = g;
-#pragma unroll
-        for (int a = 0; a < kPanel; ++a) {
+        for (int a = 0; a < kOB; ++a) {
+            const double w = (c < nprime && a < nbo) ? Wn[(int64_t)a * nprime + c] : 0.0;
             int d[kDig];
-            digits_f64(w[a], g, d);
+            digits_f64(w, g, d);
 #pragma unroll
-            for (int p = 0; p < kDig; ++p) Wd[((int64_t)p * ldw + c) * kPanel + a] = bf16_of_int(d[p]);
+            for (int p = 0; p < kDig; ++p) Wd[((int64_t)p * ldw + c) * kOB + a] = bf16_of_int(d[p]);
         }
+    }
+}
+
+// ------------------------------------------------------------------ merging the two panels' T
+
+// Partial Gram block G12(a, b) = V1(:, a)^T V2(:, b) over one row chunk per CTA (rows from
+// J0 + 32: V1 is zero-free below its diagonal there, V2 is masked). part[g][a + 32 b].
+__global__ void __launch_bounds__(256) k_gram12(const double* A, int64_t lda, int64_t s, int64_t J0, int nb2,
+                                                int64_t chunk, double* part) {
+    __shared__ double V1s[64][kPanel + 1];
+    __shared__ double V2s[64][kPanel + 1];
+    const int tid = threadIdx.x, a = tid & 31, bq = tid >> 5;   // outputs (a, 4 bq .. 4 bq + 3)
+    const int64_t rb = J0 + kPanel + (int64_t)blockIdx.x * chunk;
+    const int64_t re = rb + chunk < s ? rb + chunk : s;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t t0 = rb; t0 < re; t0 += 64) {
+        for (int i = tid; i < 64 * kPanel; i += 256) {
+            const int rr = i % 64, cc = i / 64;
+            const int64_t r = t0 + rr;
+            const bool in = r < re;
+            V1s[rr][cc] = in ? A[r + (J0 + cc) * lda] : 0.0;
+            V2s[rr][cc] = (in && cc < nb2) ? vmask(A, lda, r, J0 + kPanel, cc) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < 64; ++rr) {
+            const double v1 = V1s[rr][a];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = fma(v1, V2s[rr][4 * bq + i], acc[i]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) part[(int64_t)blockIdx.x * kPanel * kPanel + a + (4 * bq + i) * kPanel] = acc[i];
+}
+
+// Tb (kOB x kOB, column-major) = [[T1, -T1 G12 T2], [0, T2]] with G12 the sum of the partials
+// (fixed order); T1, T2 are the panels' 32 x 32 T, nb2 the second panel's width.
+__global__ void __launch_bounds__(256) k_tmerge(const double* T1, const double* T2, const double* part, int nparts,
+                                                int nb2, double* Tb) {
+    __shared__ double G[kPanel * kPanel], X[kPanel * kPanel], t1[kPanel * kPanel], t2[kPanel * kPanel];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kPanel * kPanel; i += 256) {
+        double t = 0.0;
+        for (int k = 0; k < nparts; ++k) t += part[(int64_t)k * kPanel * kPanel + i];
+        G[i] = t;
+        t1[i] = T1[i];
+        t2[i] = T2[i];
+    }
+    __syncthreads();
+    for (int i = tid; i < kPanel * kPanel; i += 256) {   // X = G12 T2
+        const int a = i % kPanel, b = i / kPanel;
+        double t = 0.0;
+        for (int k = 0; k < nb2; ++k) t += G[a + k * kPanel] * t2[k + b * kPanel];
+        X[i] = t;
+    }
+    __syncthreads();
+    for (int i = tid; i < kOB * kOB; i += 256) {
+        const int a = i % kOB, b = i / kOB;
+        double v = 0.0;
+        if (a < kPanel && b < kPanel) {
+            v = t1[a + b * kPanel];
+        } else if (a >= kPanel && b >= kPanel) {
+            v = t2[(a - kPanel) + (b - kPanel) * kPanel];
+        } else if (a < kPanel && b >= kPanel) {   // -(T1 X)(a, b - 32)
+            double t = 0.0;
+            for (int k = 0; k < kPanel; ++k) t += t1[a + k * kPanel] * X[k + (b - kPanel) * kPanel];
+            v = -t;
+        }
+        Tb[i] = v;
+    }
+}
+
+// Tb = T1 zero-padded to kOB x kOB (outer block with one panel).
+__global__ void k_tpad(const double* T1, double* Tb) {
+    for (int i = threadIdx.x; i < kOB * kOB; i += blockDim.x) {
+        const int a = i % kOB, b = i / kOB;
+        Tb[i] = (a < kPanel && b < kPanel) ? T1[a + b * kPanel] : 0.0;
     }
 }
 
 // ------------------------------------------------------------------ W = V^T C  (split over row chunks)
 
-constexpr int kVtcCols = 64;
+constexpr int kVtcCols = 32;
 constexpr int kVtcPad = 8;                     // bf16 elements of padding per k-row
 constexpr int kVtcLdk = kVtcStep + kVtcPad;    // 40
 
 struct VtcSmem {
-    unsigned short As[2][kDig][kPanel][kVtcLdk];   // V^T digits, two pipeline stages: [p][a][k]
+    unsigned short As[2][kDig][kOB][kVtcLdk];     // V^T digits, two pipeline stages: [p][a][k]
     long long Craw[2][kVtcCols][kVtcStep];        // raw fixed-point C rows, two stages: [c][k]
-    unsigned short Bs[kDig][kVtcCols][kVtcLdk];    // C digits of the current step: [q][c][k]
+    unsigned short Bs[kDig][kVtcCols][kVtcLdk];   // C digits of the current step: [q][c][k]
 };
 
 // Wp[chunk](a, c) for c in the column tile: sum over the chunk's rows of V(r, a) C(r, c).
-// Two-stage cp.async pipeline: the V^T digits and raw C rows of step k + 1 are in flight
-// while step k is cut into digits and multiplied.
+// Tile: all kOB rows of W x 32 columns, so each C digit feeds 64 outputs. Two-stage cp.async
+// pipeline: the V^T digits and raw C rows of step k + 1 are in flight while step k is cut
+// into digits and multiplied.
 __global__ void __launch_bounds__(kEmuThreads, 2)
-k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int nbw, int64_t kc,
+k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int nbo, int64_t kc,
           const unsigned short* VTd, int64_t ldv, const int* ecol, const int* E, double* Wp, int64_t nprime) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     VtcSmem& sm = *reinterpret_cast<VtcSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int64_t jc = j0 + nbw;
+    const int64_t jc = J0 + nbo;
     const int64_t c0 = (int64_t)blockIdx.x * kVtcCols;
-    const int64_t L = s - j0;
+    const int64_t L = s - J0;
     const int64_t lb = (int64_t)blockIdx.y * kc;               // local row range [lb, le)
     const int64_t le = lb + kc < L ? lb + kc : L;
-    const int mi = warp & 1, nt = warp >> 1;                   // warp: a in mi*16.., cols nt*16..
+    const int mi = warp & 3, nt = warp >> 2;                   // warp: a in mi*16.., cols nt*16..
     // Per output, the level sums are packed into two int64 fixed-point words:
     // hi = sum_{l<3} T_l 2^(8 (2 - l)), lo = sum_{l>=3} T_l 2^(8 (5 - l)); per K-step each T_l < 2^22,
     // so both stay below 2^50 over 1600 steps.
@@ -278,11 +395,11 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
 
     auto issue = [&](int stage, int64_t k0) {
         // V^T digits: per (p, a) 32 contiguous bf16 = 4 chunks of 16 B
-        for (int idx = tid; idx < kDig * kPanel * 4; idx += kEmuThreads) {
-            const int ch = idx & 3, a = (idx >> 2) % kPanel, p = (idx >> 2) / kPanel;
+        for (int idx = tid; idx < kDig * kOB * 4; idx += kEmuThreads) {
+            const int ch = idx & 3, a = (idx >> 2) % kOB, p = (idx >> 2) / kOB;
             const int64_t lr = k0 + ch * 8;
             const bool ok = lr < ldv;
-            const unsigned short* src = VTd + ((int64_t)p * kPanel + a) * ldv + (ok ? lr : 0);
+            const unsigned short* src = VTd + ((int64_t)p * kOB + a) * ldv + (ok ? lr : 0);
             cp_async16(&sm.As[stage][p][a][ch * 8], src, ok ? 16 : 0);
         }
         // raw C: per column 32 rows = 16 chunks of two int64
@@ -290,7 +407,7 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
             const int ch = idx % (kVtcStep / 2), c = idx / (kVtcStep / 2);
             const int64_t lr = k0 + 2 * ch, gc = jc + c0 + c;
             const int rows = (gc < n) ? (int)(le - lr < 0 ? 0 : (le - lr > 2 ? 2 : le - lr)) : 0;
-            const long long* src = Cfix + (rows > 0 ? (j0 + lr) + gc * lda : 0);
+            const long long* src = Cfix + (rows > 0 ? (J0 + lr) + gc * lda : 0);
             cp_async16(&sm.Craw[stage][c][2 * ch], src, rows * 8);
         }
         cp_async_commit();
@@ -303,11 +420,11 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
         else cp_async_commit();                                // keep the group count uniform
         cp_async_wait<1>();
         __syncthreads();
-        // cut this step's C entries into digits (each thread: one column, 8 rows)
+        // cut this step's C entries into digits (each thread: one column, 4 rows)
         {
-            const int c = tid >> 2, kq = (tid & 3) * 8;
+            const int c = tid >> 3, kq = (tid & 7) * 4;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
+            for (int e = 0; e < 4; ++e) {
                 int d[kDig];
                 digits_fix(sm.Craw[stage][c][kq + e], d);
 #pragma unroll
@@ -345,14 +462,14 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
     }
     cp_async_wait<0>();
     // W(a, c) = 2^(e_a + E_c - 14) sum_l 2^(-8 l) T_l   (C entries carry scale 2^(E_c - 47))
-    double* out = Wp + (int64_t)blockIdx.y * kPanel * nprime;
+    double* out = Wp + (int64_t)blockIdx.y * kOB * nprime;
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const int a = mi * 16 + g + (h >> 1) * 8;
             const int64_t col = c0 + nt * 16 + j * 8 + 2 * t + (h & 1);
-            if (col < nprime && a < nbw) {
+            if (col < nprime && a < nbo) {
                 const int sc = ecol[a] + E[jc + col] - 14;
                 const double v = ldexp((double)hi[j][h], -16) + ldexp((double)lo[j][h], -40);
                 out[(int64_t)a * nprime + col] = ldexp(v, sc);
@@ -362,7 +479,7 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, 
 
 // ------------------------------------------------------------------ C += V Wn  (exact integer update)
 
-constexpr int kUpdRows = 64, kUpdCols = 64, kUpdPad = 8, kUpdLdk = kPanel + kUpdPad;   // 40
+constexpr int kUpdRows = 64, kUpdCols = 64, kUpdPad = 8, kUpdLdk = kOB + kUpdPad;   // 72
 
 struct UpdSmem {
     unsigned short Vs[kDig][kUpdRows][kUpdLdk];   // [p][r][a]
@@ -372,19 +489,34 @@ struct UpdSmem {
     int ecol[kUpdCols];
 };
 
-__global__ void __launch_bounds__(kEmuThreads, 3)
-k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int nbw, const unsigned short* Vd,
+__global__ void __launch_bounds__(kEmuThreads, 2)
+k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int nbo, const unsigned short* Vd,
              int64_t ldv, const int* frow, const unsigned short* Wd, int64_t ldw, const int* gcol, const int* E,
              int64_t nprime) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     UpdSmem& sm = *reinterpret_cast<UpdSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int64_t jc = j0 + nbw;
-    const int64_t L = s - j0;
+    const int64_t jc = J0 + nbo;
+    const int64_t L = s - J0;
     const int64_t rb = (int64_t)blockIdx.x * kUpdRows;   // local row of tile row 0
     const int64_t cb = (int64_t)blockIdx.y * kUpdCols;   // trailing column of tile col 0
     const int wm = warp & 1, wn = warp >> 1;             // warp tile: rows wm*32..+32, cols wn*16..+16
-    // issue the loads of this warp's C entries first; they are only needed after the products
+    // digit tiles: each row of 64 bf16 is 8 chunks of 16 B
+    for (int idx = tid; idx < kDig * kUpdRows * 8; idx += kEmuThreads) {
+        const int ch = idx & 7, r = (idx >> 3) % kUpdRows, p = (idx >> 3) / kUpdRows;
+        const int64_t lr = rb + r;
+        const bool ok = lr < L;
+        cp_async16(&sm.Vs[p][r][ch * 8], Vd + ((int64_t)p * ldv + (ok ? lr : 0)) * kOB + ch * 8, ok ? 16 : 0);
+    }
+    for (int idx = tid; idx < kDig * kUpdCols * 8; idx += kEmuThreads) {
+        const int ch = idx & 7, c = (idx >> 3) % kUpdCols, q = (idx >> 3) / kUpdCols;
+        const int64_t col = cb + c;
+        const bool ok = col < nprime;
+        cp_async16(&sm.Ws[q][c][ch * 8], Wd + ((int64_t)q * ldw + (ok ? col : 0)) * kOB + ch * 8, ok ? 16 : 0);
+    }
+    cp_async_commit();
+    // this warp's C entries are loaded while the digit tiles are in flight; they are only
+    // needed after the products
     long long cval[2][2][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -394,22 +526,8 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
             for (int h = 0; h < 4; ++h) {
                 const int64_t lr = rb + wm * 32 + i * 16 + g + (h >> 1) * 8;
                 const int64_t col = cb + wn * 16 + j * 8 + 2 * t + (h & 1);
-                cval[i][j][h] = (lr < L && col < nprime) ? Cfix[(j0 + lr) + (jc + col) * lda] : 0LL;
+                cval[i][j][h] = (lr < L && col < nprime) ? Cfix[(J0 + lr) + (jc + col) * lda] : 0LL;
             }
-    // digit tiles: each row of 32 bf16 is 4 chunks of 16 B
-    for (int idx = tid; idx < kDig * kUpdRows * 4; idx += kEmuThreads) {
-        const int ch = idx & 3, r = (idx >> 2) % kUpdRows, p = (idx >> 2) / kUpdRows;
-        const int64_t lr = rb + r;
-        const bool ok = lr < L;
-        cp_async16(&sm.Vs[p][r][ch * 8], Vd + ((int64_t)p * ldv + (ok ? lr : 0)) * kPanel + ch * 8, ok ? 16 : 0);
-    }
-    for (int idx = tid; idx < kDig * kUpdCols * 4; idx += kEmuThreads) {
-        const int ch = idx & 3, c = (idx >> 2) % kUpdCols, q = (idx >> 2) / kUpdCols;
-        const int64_t col = cb + c;
-        const bool ok = col < nprime;
-        cp_async16(&sm.Ws[q][c][ch * 8], Wd + ((int64_t)q * ldw + (ok ? col : 0)) * kPanel + ch * 8, ok ? 16 : 0);
-    }
-    cp_async_commit();
     for (int i = tid; i < kUpdRows; i += kEmuThreads) sm.frow[i] = rb + i < L ? frow[rb + i] : 0;
     for (int i = tid; i < kUpdCols; i += kEmuThreads) {
         sm.gcol[i] = cb + i < nprime ? gcol[cb + i] : 0;
@@ -417,6 +535,7 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
     }
     cp_async_wait<0>();
     __syncthreads();
+    const int kmax = nbo > kPanel ? kOB : kPanel;   // zero digits past nbo need no products
     long long acc64[2][2][4];
 #pragma unroll 1
     for (int l = 0; l <= kLev; ++l) {
@@ -426,11 +545,10 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int h = 0; h < 4; ++h) acc[i][j][h] = kMagic;
+                for (int h = 0; h < 4; ++h) acc[i][j][h] = 0.0f;
         for (int p = 0; p <= l; ++p) {
             const int q = l - p;
-#pragma unroll
-            for (int ks = 0; ks < kPanel; ks += 16) {
+            for (int ks = 0; ks < kmax; ks += 16) {
                 uint32_t af[2][4], bq[4];
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
@@ -443,13 +561,14 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
                     for (int j = 0; j < 2; ++j) hmma(acc[i][j], af[i], bfr[j]);
             }
         }
+        // every level sum is an integer below 6 x 64 x 2^14 < 2^24: exact in FP32
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int j = 0; j < 2; ++j)
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    const long long v = (long long)magic_to_int(acc[i][j][h]);
+                    const long long v = (long long)__float2int_rn(acc[i][j][h]);
                     acc64[i][j][h] = l == 0 ? v : (acc64[i][j][h] << 8) + v;
                 }
     }
@@ -470,7 +589,7 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
                     if (v == 0) dlt = 0;
                     else if (sh >= 0) dlt = sh < 63 ? v << sh : 0;
                     else dlt = -sh < 63 ? (v + (1LL << (-sh - 1))) >> (-sh) : 0;
-                    Cfix[(j0 + lr) + (jc + col) * lda] = cval[i][j][h] + dlt;
+                    Cfix[(J0 + lr) + (jc + col) * lda] = cval[i][j][h] + dlt;
                 }
             }
 }
@@ -479,46 +598,57 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t j0, int
 
 struct EmuScratch {
     int* E;                       // n column exponents
-    unsigned long long* colmax;   // kPanel
-    int* ecol;                    // kPanel
+    unsigned long long* colmax;   // kOB
+    int* ecol;                    // kOB
     int* frow;                    // s
     int* gcol;                    // n
-    unsigned short* Vd;           // kDig * s * kPanel
-    unsigned short* VTd;          // kDig * kPanel * s
-    unsigned short* Wd;           // kDig * n * kPanel
+    unsigned short* Vd;           // kDig * s * kOB
+    unsigned short* VTd;          // kDig * kOB * s
+    unsigned short* Wd;           // kDig * n * kOB
+    double* Wp;                   // split-K partials of W (kOB x n per chunk)
+    int64_t wp_elems;
+    double* Wn;                   // kOB x n
+    double* T1;                   // first panel's T (32 x 32)
+    double* Tb;                   // outer block's T (kOB x kOB)
+    double* gpart;                // Gram partials of the two panels
+    int64_t gparts;
 };
 
-size_t qr_emu_scratch_bytes(int64_t s, int64_t n) {
-    Carve c{nullptr, 0, 0, true};
-    const int64_t ldv = round_up(s, 8), ldw = round_up(n, 8);
-    c.take<int>((size_t)n);
-    c.take<unsigned long long>(kPanel);
-    c.take<int>(kPanel);
-    c.take<int>((size_t)ldv);
-    c.take<int>((size_t)ldw);
-    c.take<unsigned short>((size_t)(kDig * ldv * kPanel));
-    c.take<unsigned short>((size_t)(kDig * ldv * kPanel));
-    c.take<unsigned short>((size_t)(kDig * ldw * kPanel));
-    return c.off;
+static int64_t emu_wp_elems(int64_t n) {
+    const int64_t a = (int64_t)kOB * (n + kVtcCols);
+    const int64_t b = (int64_t)kOB * kVtcCols * (8LL * device_sm_count() + 8);
+    return a > b ? a : b;
 }
 
 static EmuScratch emu_carve(Carve& c, int64_t s, int64_t n) {
     const int64_t ldv = round_up(s, 8), ldw = round_up(n, 8);
     EmuScratch e;
     e.E = c.take<int>((size_t)n);
-    e.colmax = c.take<unsigned long long>(kPanel);
-    e.ecol = c.take<int>(kPanel);
+    e.colmax = c.take<unsigned long long>(kOB);
+    e.ecol = c.take<int>(kOB);
     e.frow = c.take<int>((size_t)ldv);
     e.gcol = c.take<int>((size_t)ldw);
-    e.Vd = c.take<unsigned short>((size_t)(kDig * ldv * kPanel));
-    e.VTd = c.take<unsigned short>((size_t)(kDig * ldv * kPanel));
-    e.Wd = c.take<unsigned short>((size_t)(kDig * ldw * kPanel));
+    e.Vd = c.take<unsigned short>((size_t)(kDig * ldv * kOB));
+    e.VTd = c.take<unsigned short>((size_t)(kDig * ldv * kOB));
+    e.Wd = c.take<unsigned short>((size_t)(kDig * ldw * kOB));
+    e.wp_elems = emu_wp_elems(n);
+    e.Wp = c.take<double>((size_t)e.wp_elems);
+    e.Wn = c.take<double>((size_t)(kOB * (n + kOB)));
+    e.T1 = c.take<double>(kPanel * kPanel);
+    e.Tb = c.take<double>(kOB * kOB);
+    e.gparts = 2LL * device_sm_count();
+    e.gpart = c.take<double>((size_t)(e.gparts * kPanel * kPanel));
     return e;
+}
+
+size_t qr_emu_scratch_bytes(int64_t s, int64_t n) {
+    Carve c{nullptr, 0, 0, true};
+    emu_carve(c, s, n);
+    return c.off;
 }
 
 int qr_panel_launch_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, const QrScratch& q, int* err,
                         long long spin, cudaStream_t st);
-int qr_wreduce_launch_f64(const QrScratch& q, int ks, int nbw, int64_t nprime, cudaStream_t st);
 
 int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, void* emu_work,
                       size_t emu_bytes, int* err, long long spin, cudaStream_t st, int64_t* launches) {
@@ -526,13 +656,15 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     if (emu_bytes < qr_emu_scratch_bytes(s, n)) return CSLS_ERR_WORKSPACE;
     Carve c{(char*)emu_work, 0, emu_bytes, false};
     EmuScratch e = emu_carve(c, s, n);
-    const int64_t ldv = round_up(s, 8), ldw = round_up(n, 8);
+    const int64_t ldv = round_up(s, 8);
     static bool attr = false;
     if (!attr) {
         CSLS_CUDA(cudaFuncSetAttribute(k_emu_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(VtcSmem)));
         CSLS_CUDA(cudaFuncSetAttribute(k_emu_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpdSmem)));
+        CSLS_CUDA(cudaFuncSetAttribute(k_wreduce_ob, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWrSmem));
         attr = true;
     }
+    (void)ldv;
     const int sms = device_sm_count();
     CSLS_CUDA(cudaMemsetAsync(q.bar, 0, sizeof(GridBarrier), st));
     k_col_exponent<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, st>>>(A, lda, s, n, e.E);
@@ -541,61 +673,87 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     k_to_fixed<<<fg, 256, 0, st>>>(A, lda, s, n, e.E);
     CSLS_CUDA(cudaGetLastError());
     int64_t nl = 2;
-    for (int64_t j0 = 0; j0 < n; j0 += kPanel) {
-        const int nbw = (int)(n - j0 < kPanel ? n - j0 : kPanel);
-        const int64_t L = s - j0;
-        dim3 pg((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 256), 256)), (unsigned)nbw);
-        k_panel_to_f64<<<pg, 256, 0, st>>>(A, lda, s, j0, nbw, e.E);
+    for (int64_t J0 = 0; J0 < n; J0 += kOB) {
+        const int nbo = (int)(n - J0 < kOB ? n - J0 : kOB);
+        const int nb1 = nbo < kPanel ? nbo : kPanel;
+        const int nb2 = nbo - nb1;
+        const int64_t L = s - J0;
+        // the outer block's columns return to binary64 (rows below and above the diagonal block)
+        dim3 pg((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 256), 256)), (unsigned)nbo);
+        k_panel_to_f64<<<pg, 256, 0, st>>>(A, lda, s, J0, nbo, e.E);
         CSLS_CUDA(cudaGetLastError());
-        if (j0 > 0) {
-            dim3 tg((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(j0, 256), 64)), (unsigned)nbw);
-            k_panel_top_to_f64<<<tg, 256, 0, st>>>(A, lda, j0, nbw, e.E);
+        if (J0 > 0) {
+            dim3 tg((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(J0, 256), 64)), (unsigned)nbo);
+            k_panel_top_to_f64<<<tg, 256, 0, st>>>(A, lda, J0, nbo, e.E);
             CSLS_CUDA(cudaGetLastError());
         }
-        {
-            const int tk = kt_begin(kFamPanel, st);
-            CSLS_TRY(qr_panel_launch_f64(A, lda, s, j0, nbw, q, err, spin, st));
-            kt_end(tk, 0.0, st);
-        }
+        // first panel, its update of the second one (FP64 MMA), second panel
+        int tk = kt_begin(kFamPanel, st);
+        CSLS_TRY(qr_panel_launch_f64(A, lda, s, J0, nb1, q, err, spin, st));
+        kt_end(tk, 0.0, st);
         nl += 3;
-        const int64_t nprime = n - j0 - nbw;
+        if (nb2 > 0) {
+            CSLS_CUDA(cudaMemcpyAsync(e.T1, q.T, sizeof(double) * kPanel * kPanel, cudaMemcpyDeviceToDevice, st));
+            CSLS_TRY(qr_trailing_update_f64(A, lda, s, J0 + nbo, J0, nb1, q, st));
+            tk = kt_begin(kFamPanel, st);
+            CSLS_TRY(qr_panel_launch_f64(A, lda, s, J0 + kPanel, nb2, q, err, spin, st));
+            kt_end(tk, 0.0, st);
+            // merged T of the outer block
+            const int64_t L2 = s - J0 - kPanel;
+            int gp = (int)std::min<int64_t>(e.gparts, std::max<int64_t>(1, ceil_div(L2, 512)));
+            const int64_t chunk = round_up(ceil_div(L2, gp), 64);
+            gp = (int)ceil_div(L2, chunk);
+            k_gram12<<<gp, 256, 0, st>>>(A, lda, s, J0, nb2, chunk, e.gpart);
+            CSLS_CUDA(cudaGetLastError());
+            k_tmerge<<<1, 256, 0, st>>>(e.T1, q.T, e.gpart, gp, nb2, e.Tb);
+            CSLS_CUDA(cudaGetLastError());
+            nl += 6;
+        } else {
+            k_tpad<<<1, 256, 0, st>>>(q.T, e.Tb);
+            CSLS_CUDA(cudaGetLastError());
+            nl += 1;
+        }
+        const int64_t nprime = n - J0 - nbo;
         if (nprime <= 0) continue;
         // digits of V
-        CSLS_CUDA(cudaMemsetAsync(e.colmax, 0, sizeof(unsigned long long) * kPanel, st));
-        k_vcolmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 8), (int64_t)sms * 4)), 256, 0, st>>>(
-            A, lda, s, j0, nbw, e.colmax);
+        CSLS_CUDA(cudaMemsetAsync(e.colmax, 0, sizeof(unsigned long long) * kOB, st));
+        k_vcolmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 4), (int64_t)sms * 4)), 256, 0, st>>>(
+            A, lda, s, J0, nbo, e.colmax);
         CSLS_CUDA(cudaGetLastError());
-        const int64_t ldvp = round_up(L, 8);   // digit planes use the current panel height
+        const int64_t ldvp = round_up(L, 8);   // digit planes use the current block height
         k_vdigits<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ldvp, 256), (int64_t)sms * 8)), 256, 0, st>>>(
-            A, lda, s, j0, nbw, e.colmax, ldvp, e.Vd, e.VTd, e.frow, e.ecol);
+            A, lda, s, J0, nbo, e.colmax, ldvp, e.Vd, e.VTd, e.frow, e.ecol);
         CSLS_CUDA(cudaGetLastError());
         // W = V^T C over row chunks
         const int64_t ntn = ceil_div(nprime, kVtcCols);
         int64_t ks = ceil_div(8LL * sms, ntn);
         const int64_t maxks = ceil_div(L, kVtcStep);
         if (ks > maxks) ks = maxks;
+        if (ks > 64) ks = 64;   // narrow trailing blocks: a few long row chunks keep the partial sums short
         if (ks < 1) ks = 1;
-        while (ks > 1 && ks * kPanel * ntn * kVtcCols > q.wp_elems) --ks;
+        while (ks > 1 && ks * kOB * ntn * kVtcCols > e.wp_elems) --ks;
         const int64_t kc = round_up(ceil_div(L, ks), kVtcStep);
         ks = ceil_div(L, kc);
-        const double prod_flop = 2.0 * (double)L * (double)nprime * (double)nbw;
-        int tk = kt_begin(kFamVtc, st);
+        const double prod_flop = 2.0 * (double)L * (double)nprime * (double)nbo;
+        tk = kt_begin(kFamVtc, st);
         k_emu_vtc<<<dim3((unsigned)ntn, (unsigned)ks), kEmuThreads, sizeof(VtcSmem), st>>>(
-            reinterpret_cast<const long long*>(A), lda, s, n, j0, nbw, kc, e.VTd, ldvp, e.ecol, e.E, q.Wp, nprime);
+            reinterpret_cast<const long long*>(A), lda, s, n, J0, nbo, kc, e.VTd, ldvp, e.ecol, e.E, e.Wp, nprime);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
-        CSLS_TRY(qr_wreduce_launch_f64(q, (int)ks, nbw, nprime, st));
+        k_wreduce_ob<<<(unsigned)ceil_div(nprime, kWrCols), 256, kWrSmem, st>>>(e.Wp, (int)ks, e.Tb, nbo, e.Wn, nprime);
+        CSLS_CUDA(cudaGetLastError());
         // digits of Wn, then the exact update
         const int64_t ldwp = round_up(nprime, 8);
-        k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 256)), 256, 0, st>>>(q.Wn, nprime, ldwp, e.Wd, e.gcol);
+        k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 256)), 256, 0, st>>>(e.Wn, nbo, nprime, ldwp, e.Wd,
+                                                                                        e.gcol);
         CSLS_CUDA(cudaGetLastError());
         tk = kt_begin(kFamUpdate, st);
         k_emu_update<<<dim3((unsigned)ceil_div(L, kUpdRows), (unsigned)ceil_div(nprime, kUpdCols)), kEmuThreads,
-                       sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n, j0, nbw, e.Vd, ldvp,
+                       sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n, J0, nbo, e.Vd, ldvp,
                                               e.frow, e.Wd, ldwp, e.gcol, e.E, nprime);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
-        nl += 6;
+        nl += 7;
     }
     if (launches) *launches += nl;
     return CSLS_OK;
