@@ -489,6 +489,8 @@ struct UpdSmem {
     int ecol[kUpdCols];
 };
 
+// KM: products over the first KM digit columns (64, or 32 when the outer block has one panel).
+template <int KM>
 __global__ void __launch_bounds__(kEmuThreads, 2)
 k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int nbo, const unsigned short* Vd,
              int64_t ldv, const int* frow, const unsigned short* Wd, int64_t ldw, const int* gcol, const int* E,
@@ -535,7 +537,6 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int
     }
     cp_async_wait<0>();
     __syncthreads();
-    const int kmax = nbo > kPanel ? kOB : kPanel;   // zero digits past nbo need no products
     long long acc64[2][2][4];
 #pragma unroll 1
     for (int l = 0; l <= kLev; ++l) {
@@ -548,7 +549,8 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int
                 for (int h = 0; h < 4; ++h) acc[i][j][h] = 0.0f;
         for (int p = 0; p <= l; ++p) {
             const int q = l - p;
-            for (int ks = 0; ks < kmax; ks += 16) {
+#pragma unroll
+            for (int ks = 0; ks < KM; ks += 16) {
                 uint32_t af[2][4], bq[4];
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
@@ -660,7 +662,10 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     static bool attr = false;
     if (!attr) {
         CSLS_CUDA(cudaFuncSetAttribute(k_emu_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(VtcSmem)));
-        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpdSmem)));
+        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kOB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(UpdSmem)));
+        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kPanel>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(UpdSmem)));
         CSLS_CUDA(cudaFuncSetAttribute(k_wreduce_ob, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWrSmem));
         attr = true;
     }
@@ -748,9 +753,15 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
                                                                                         e.gcol);
         CSLS_CUDA(cudaGetLastError());
         tk = kt_begin(kFamUpdate, st);
-        k_emu_update<<<dim3((unsigned)ceil_div(L, kUpdRows), (unsigned)ceil_div(nprime, kUpdCols)), kEmuThreads,
-                       sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n, J0, nbo, e.Vd, ldvp,
-                                              e.frow, e.Wd, ldwp, e.gcol, e.E, nprime);
+        const dim3 ug((unsigned)ceil_div(L, kUpdRows), (unsigned)ceil_div(nprime, kUpdCols));
+        if (nbo > kPanel)   // zero digits past nbo need no products
+            k_emu_update<kOB><<<ug, kEmuThreads, sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n, J0,
+                                                                        nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp, e.gcol,
+                                                                        e.E, nprime);
+        else
+            k_emu_update<kPanel><<<ug, kEmuThreads, sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n,
+                                                                           J0, nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp,
+                                                                           e.gcol, e.E, nprime);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
         nl += 7;
