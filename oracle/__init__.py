@@ -267,6 +267,46 @@ class _Csr1:
         return int(self.row_ptr[-1])
 
 
+def form_b(A, fac):
+    """The explicit preconditioned matrix of Algorithm 1 step 4 / Algorithm 2 step 4: B = A R^-1 (each
+    row b_i solves R^T b_i = a_i by substitution) or B = A P. Dense m x r, column-major."""
+    Ad = np.zeros((A.m, A.n))
+    rows = np.repeat(np.arange(A.m), np.diff(A.row_ptr))
+    Ad[rows, A.col] = A.val
+    if fac["kind"] == "svd":
+        return np.asfortranarray(Ad @ fac["F"])
+    R = fac["R"]
+    B = np.empty((A.m, A.n), order="F")
+    for i in range(A.m):
+        B[i, :] = trsv_upper_trans(R, Ad[i, :])
+    return B
+
+
+class _Dense:
+    """A dense matrix as CSR with every entry stored (for the oracle's LSQR on B)."""
+
+    def __init__(self, B):
+        m, n = B.shape
+        self.m, self.n = m, n
+        self.row_ptr = np.arange(m + 1, dtype=np.int64) * n
+        self.col = np.tile(np.arange(n, dtype=np.int32), m)
+        self.val = np.ascontiguousarray(B).reshape(-1)
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+
+def explicit_lsqr(A, b, fac, tol=1e-12, maxit=None, fixed_iters=0):
+    """LSQR on the formed B (Algorithm 1 step 5), then x = R^-1 y or P y (step 6). Returns (x, y, info)."""
+    B = form_b(A, fac)
+    r = B.shape[1]
+    y, info = lsqr(_Dense(B), b, np.eye(r), "qr", atol=tol, btol=tol,
+                   maxit=(A.n if maxit is None else maxit), fixed_iters=fixed_iters)
+    x = fac["F"] @ y if fac["kind"] == "svd" else trsv_upper(fac["R"], y)
+    return x, y, info
+
+
 def csqrp_lsqr(A, b, gamma=4.0, s=None, seed=1, variant="qr", prec="f64", tol=1e-12, maxit=None,
                fixed_iters=0, history=False, warm=False):
     """Full CSQRP-LSQR (Algorithm 1) / CSSVDP-LSQR (Algorithm 2) in the implicit form; with warm=True

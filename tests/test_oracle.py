@@ -427,3 +427,34 @@ def test_warm_start_fewer_iterations_same_solution_cfg1():
     spread = np.linalg.norm(Ad @ (x_hh - xc)) / np.linalg.norm(Ad @ xc)
     assert np.linalg.norm(Ad @ (xw - xc)) <= max(1e-10, 2 * spread) * np.linalg.norm(Ad @ xc)
     assert abs(np.linalg.norm(p.b[0] - Ad @ xw) - np.linalg.norm(p.b[0] - Ad @ xc)) <= 1e-12 * np.linalg.norm(p.b[0])
+
+
+# ----------------------------------------------------------------------------- explicit form (Algorithm 1 step 4)
+
+def test_explicit_b_times_r_is_a_and_well_conditioned():
+    """B = A R^-1 formed row by row satisfies B R = A, and cond(B) stays below 10 (Theorem 3.2)."""
+    p = config_problem("cfg1")
+    fac = oracle.factor(p, 4 * p.n, 11)
+    B = oracle.form_b(p, fac)
+    Ad = p.dense()
+    assert np.linalg.norm(B @ fac["R"] - Ad) <= 1e-12 * np.linalg.norm(Ad)
+    sv = np.linalg.svd(B, compute_uv=False)
+    assert sv[0] / sv[-1] < 10
+
+
+def test_explicit_form_solution_matches_direct_and_implicit():
+    p = config_problem("cfg1")
+    fac = oracle.factor(p, 4 * p.n, 11)
+    x, y, info = oracle.explicit_lsqr(p, p.b[0], fac)
+    Ad = p.dense()
+    x_hh, _ = oracle.hhqr_solve(Ad, p.b[0])
+    _, xi, _ = oracle.csqrp_lsqr(p, p.b[0], seed=11)
+    spread = np.linalg.norm(Ad @ (x_hh - xi)) / np.linalg.norm(Ad @ xi)
+    assert np.linalg.norm(Ad @ (x - x_hh)) <= max(1e-10, 2 * spread) * np.linalg.norm(Ad @ x_hh)
+    assert info["istop"] in (1, 2)
+    # M = I on a tiny exact problem: the explicit form with R = I is plain LSQR
+    rng = np.random.default_rng(2)
+    A = random_sparse(60, 5, 3, rng)
+    b = rng.standard_normal(60)
+    x1, _, _ = oracle.explicit_lsqr(A, b, dict(kind="qr", R=np.eye(5), F=np.eye(5)), tol=1e-15, maxit=50)
+    np.testing.assert_allclose(x1, np.linalg.lstsq(A.dense(), b, rcond=None)[0], rtol=1e-10, atol=1e-12)
