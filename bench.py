@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--prec", default="f64emu", choices=["f64", "f32", "f64emu"])
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 solve timed beside")
     ap.add_argument("--config", default="cfg2")
+    ap.add_argument("--explicit", action="store_true",
+                    help="the explicit form: B = A R^-1 formed densely, LSQR on B (Algorithm 1 steps 4-6)")
     ap.add_argument("--warm", action="store_true",
                     help="start LSQR from the sketch-and-solve point R^-1 Q^T S b (Remark 3.1)")
     ap.add_argument("--variant", default="qr", choices=["qr", "svd"],
@@ -311,6 +313,17 @@ def main():
     def step(time_kernels=0):
         # time_kernels: the factor brackets each launch of its QR kernel families with CUDA
         # events on its stream (the per-kernel roofline below)
+        if args.explicit:
+            F = csls.csls_factor(A, time_kernels=time_kernels, **opts)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            Bt = csls.csls_form_b(F, A)
+            f1.record(stream)
+            x, rep = csls.csls_solve_explicit(F, Bt, b, raise_on_error=False, **opts)
+            torch.cuda.synchronize()
+            rep["ms_form_b"] = f0.elapsed_time(f1)
+            del Bt
+            return F, x, rep
         if args.warm:
             F, x0 = csls.csls_factor_warm(A, b, time_kernels=time_kernels, **opts)
             x, rep = csls.csls_solve(F, A, b, x=x0, warm_start=1, raise_on_error=False, **opts)
@@ -427,7 +440,12 @@ def main():
         A2 = csls.Csr(h_row.cuda(non_blocking=True), h_col.cuda(non_blocking=True), h_val.cuda(non_blocking=True),
                       m, n)
         b2 = h_b.cuda(non_blocking=True)
-        if args.warm:
+        if args.explicit:
+            F2 = csls.csls_factor(A2, **opts)
+            B2 = csls.csls_form_b(F2, A2)
+            x2, _ = csls.csls_solve_explicit(F2, B2, b2, raise_on_error=False, **opts)
+            del B2
+        elif args.warm:
             F2, x0 = csls.csls_factor_warm(A2, b2, **opts)
             x2, _ = csls.csls_solve(F2, A2, b2, x=x0, warm_start=1, raise_on_error=False, **opts)
         else:
@@ -507,11 +525,13 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": nnz, "s": s, "tol": 1e-12,
                        "variant": args.variant, "start": "R^-1 Q^T S b" if args.warm else "0",
+                       "form": "explicit B = A R^-1" if args.explicit else "implicit (per-step triangular solves)",
                        "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (dense sketch 5.2 GB, A 173 MB)"},
             "status": csls.STATUS_NAMES.get(status, status), "iterations": int(statistics.median(iters)),
             "phase_ms": {"sketch": statistics.median(sketch_ms), "factor": statistics.median(qr_ms),
-                         "solve": statistics.median(solve_ms)},
+                         "solve": statistics.median(solve_ms),
+                         **({"form_b": rep.get("ms_form_b")} if args.explicit else {})},
             "roofline": roofline,
             "spmv_pair": {"bound": "hbm", "achieved": pair_gbs, "peak": hbm, "unit": "GB/s", "frac": pair_gbs / hbm,
                           "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src + " copy (read + write)",

@@ -240,6 +240,24 @@ int csls_solve_backward(const csls_factor_t* factor, const csls_csr* A, const do
                         const csls_opts* opts, void* work, size_t work_bytes, csls_report* rep,
                         csls_stream_t stream);
 
+/* ---------------------------------------------------------------- explicit form */
+/* The paper's explicit form (Algorithm 1 / 2 steps 4-6): B = A R^-1 (QR variant) or B = A P
+ * (SVD variant) formed as a dense m x r matrix, LSQR on B, x = R^-1 y or P y. It costs
+ * m n^2 flops to form B (a right-side triangular solve on the densified A) and a dense
+ * m x r pass per product, against the per-step triangular solves of csls_solve; it is
+ * there to compare the two forms.
+ * csls_form_b: B (device, column-major, ld ldb >= m, r columns; caller-owned, fully
+ * written). QR variant needs a binary64 R (CSLS_ERR_ARG for a binary32 factor).
+ * csls_solve_explicit: one right-hand side b (m) -> x (n); opts as for csls_solve
+ * (warm_start ignored); rep as for csls_solve. */
+int csls_form_b_workspace(const csls_factor_t* factor, size_t* bytes);
+int csls_form_b(const csls_factor_t* factor, const csls_csr* A, double* B, int64_t ldb, void* work,
+                size_t work_bytes, csls_stream_t stream);
+int csls_solve_explicit_workspace(const csls_factor_t* factor, size_t* bytes);
+int csls_solve_explicit(const csls_factor_t* factor, const double* B, int64_t ldb, const double* b,
+                        double* x, const csls_opts* opts, void* work, size_t work_bytes,
+                        csls_report* rep, csls_stream_t stream);
+
 /* ---------------------------------------------------------------- batches */
 /* Many independent problems of uneven size, each with its own factor (built by
  * csls_factor): all LSQR recurrences advance together in batched kernels whose

@@ -76,6 +76,13 @@ EXPORTS = {
                                         ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "csls_factor_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "csls_form_b_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "csls_form_b": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "csls_solve_explicit_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "csls_solve_explicit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "csls_factor_view": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
     "csls_precond_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -308,6 +315,38 @@ def csls_factor_warm(A, b, opts=None, stream=None, **kw):
     del temp
     _check(st, "csls_factor_warm")
     return Factor(handle, persist, A, opts, rep.as_dict()), x0
+
+
+def csls_form_b(F, A, stream=None):
+    """B = A R^-1 (or A P) as a dense tensor; returns the (r, m) row-major view of the column-major B."""
+    v = F.view()
+    r = v["r"]
+    B = torch.empty((r, A.m), dtype=torch.float64, device=A.val.device)
+    nbytes = ctypes.c_size_t()
+    _check(_lib().csls_form_b_workspace(F.handle, ctypes.byref(nbytes)), "csls_form_b_workspace")
+    work = _workspace(nbytes.value, A.val.device)
+    a = A.struct()
+    _check(_lib().csls_form_b(F.handle, ctypes.byref(a), _ptr(B), A.m, _ptr(work), work.numel(), _stream(stream)),
+           "csls_form_b")
+    return B
+
+
+def csls_solve_explicit(F, B, b, opts=None, stream=None, raise_on_error=True, **kw):
+    """LSQR on the formed B (from csls_form_b), x = R^-1 y or P y; returns (x, report dict)."""
+    opts = opts or make_opts(**kw)
+    m = B.shape[1]
+    x = torch.empty(F.view()["n"], dtype=torch.float64, device=b.device)
+    nbytes = ctypes.c_size_t()
+    _check(_lib().csls_solve_explicit_workspace(F.handle, ctypes.byref(nbytes)), "csls_solve_explicit_workspace")
+    work = _workspace(nbytes.value, b.device)
+    rep = csls_report()
+    st = _lib().csls_solve_explicit(F.handle, _ptr(B), m, _ptr(b.contiguous()), _ptr(x), ctypes.byref(opts),
+                                    _ptr(work), work.numel(), ctypes.byref(rep), _stream(stream))
+    if raise_on_error:
+        _check(st, "csls_solve_explicit")
+    out = rep.as_dict()
+    out["status"] = st
+    return x, out
 
 
 def csls_precond_apply(F, v, trans=False, stream=None):

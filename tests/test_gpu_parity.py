@@ -486,3 +486,57 @@ def test_warm_start_argument_errors(csls):
     F = csls.csls_factor(A, seed=1)
     _, _, st = csls.csls_batch_solve([F], [A], [b], warm_start=1, raise_on_error=False)
     assert st == 1
+
+
+# ----------------------------------------------------------------------------- explicit form (Algorithm 1 steps 4-6)
+
+def test_explicit_form_well_conditioned_matches_oracle(csls):
+    rng = np.random.default_rng(41)
+    Acpu = random_sparse(2500, 150, 8, rng)   # 3 diagonal blocks (ragged), 40 row tiles (ragged)
+    b = rng.standard_normal(2500)
+    A = dev(csls, Acpu)
+    F = csls.csls_factor(A, s=600, seed=6)
+    B = csls.csls_form_b(F, A).cpu().numpy().T
+    fac = oracle.factor(Acpu, 600, 6)
+    Bo = oracle.form_b(Acpu, fac)
+    assert _rel(B, Bo) < 1e-10
+    for k in (1, 4):
+        x, _ = csls.csls_solve_explicit(F, torch.tensor(B.T.copy(), device="cuda"), torch.tensor(b, device="cuda"),
+                                        fixed_iters=k)
+        xo, _, _ = oracle.explicit_lsqr(Acpu, b, fac, fixed_iters=k)
+        assert _rel(x.cpu().numpy(), xo) < 1e-10
+
+
+def test_explicit_form_rfm(csls):
+    p = SKETCH_CASES["cfg1"]()
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=11)
+    Bt = csls.csls_form_b(F, A)
+    B = Bt.cpu().numpy().T
+    Ad = p.dense()
+    R = F.R().cpu().numpy()
+    assert np.linalg.norm(B @ R - Ad) <= 1e-12 * np.linalg.norm(Ad)   # B R = A with this factor's R
+    sv = np.linalg.svd(B, compute_uv=False)
+    assert sv[0] / sv[-1] < 10                                          # Theorem 3.2
+    x, rep = csls.csls_solve_explicit(F, Bt, torch.tensor(p.b[0], device="cuda"))
+    fac = oracle.factor(p, 4 * p.n, 11)
+    xo, _, _ = oracle.explicit_lsqr(p, p.b[0], fac)
+    x_hh, _ = oracle.hhqr_solve(Ad, p.b[0])
+    _, xi, _ = oracle.csqrp_lsqr(p, p.b[0], seed=11)
+    spread = max(_anorm_rel(Ad, x_hh, xo), _anorm_rel(Ad, x_hh, xi))
+    assert _anorm_rel(Ad, x.cpu().numpy(), xo) <= max(1e-10, 2 * spread)
+    assert rep["istop"] in (1, 2) and rep["cond_est"] < 10
+
+
+def test_explicit_form_svd_rank_deficient(csls):
+    from workloads import table_c1_problem
+    p = table_c1_problem("rel6")
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=3, variant="svd")
+    Bt = csls.csls_form_b(F, A)
+    assert Bt.shape[0] == p.info["rank"]
+    x, rep = csls.csls_solve_explicit(F, Bt, torch.tensor(p.b[0], device="cuda"), tol=1e-14, maxit=500)
+    Ad = p.dense()
+    x_mn = np.linalg.lstsq(Ad, p.b[0], rcond=None)[0]
+    assert np.linalg.norm(x.cpu().numpy() - x_mn) <= 1e-8 * np.linalg.norm(x_mn)
+    assert rep["cond_est"] < 10
