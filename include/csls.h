@@ -240,6 +240,30 @@ int csls_solve_backward(const csls_factor_t* factor, const csls_csr* A, const do
                         const csls_opts* opts, void* work, size_t work_bytes, csls_report* rep,
                         csls_stream_t stream);
 
+/* ---------------------------------------------------------------- RFM assembly */
+/* One row of a random-feature-method system for the Poisson problem (Section 2.1):
+ * kind 0 = -Laplace u at the local point t of `box`, 1 = the value u (boundary row),
+ * 2 = C0 jump u(box) - u(nbox) and 3 = C1 jump of d u / d x_axis across the `axis` face
+ * where box's local point is t (t[axis] = +1) and nbox's is t with t[axis] = -1.
+ * Unused fields are ignored (t[2] in 2D; nbox, axis for kinds 0-1). */
+typedef struct {
+    int32_t kind, box, nbox, axis;
+    double t[3];
+} csls_rfm_row;
+
+/* The CSR matrix of an RFM system on the device: box i carries J features
+ * tanh(k_ij . l_i(x) + c_ij) with l_i the affine map of the box onto [-1, 1]^dim of
+ * half-widths r_half (host, dim entries); k (device, boxes x J x dim, feature-major) and
+ * c (device, boxes x J). rows (device, nrows descriptors) fix the row order. Output (device,
+ * caller-owned): row_ptr (nrows + 1), col and val (sum of the widths: J per row of kinds
+ * 0-1, 2 J for 2-3; columns box-major, ascending within each row). Scratch: the
+ * csls_rfm_assemble_workspace bytes. Errors: CSLS_ERR_ARG (dim not 2 or 3, J <= 0,
+ * non-positive half-widths, NULL pointers). */
+int csls_rfm_assemble_workspace(int64_t nrows, size_t* bytes);
+int csls_rfm_assemble(int dim, const double* r_half, int64_t J, const double* k, const double* c,
+                      int64_t nrows, const csls_rfm_row* rows, int64_t* row_ptr, int32_t* col,
+                      double* val, void* work, size_t work_bytes, csls_stream_t stream);
+
 /* ---------------------------------------------------------------- explicit form */
 /* The paper's explicit form (Algorithm 1 / 2 steps 4-6): B = A R^-1 (QR variant) or B = A P
  * (SVD variant) formed as a dense m x r matrix, LSQR on B, x = R^-1 y or P y. It costs

@@ -540,3 +540,46 @@ def test_explicit_form_svd_rank_deficient(csls):
     x_mn = np.linalg.lstsq(Ad, p.b[0], rcond=None)[0]
     assert np.linalg.norm(x.cpu().numpy() - x_mn) <= 1e-8 * np.linalg.norm(x_mn)
     assert rep["cond_est"] < 10
+
+
+# ----------------------------------------------------------------------------- RFM assembly on the device
+
+def _assemble_on_device(csls, p):
+    from workloads import rfm_row_descriptors
+    rows = rfm_row_descriptors(p)
+    rows_dev = torch.from_numpy(rows.view(np.uint8).copy()).cuda()
+    k = torch.tensor(p.k, device="cuda")
+    c = torch.tensor(p.c, device="cuda")
+    r_half = 0.5 / np.asarray(p.grid, dtype=np.float64)
+    return csls.csls_rfm_assemble(p.dim, r_half, p.J, k, c, rows_dev)
+
+
+@pytest.mark.parametrize("case", ["cfg1", "ragged2d", "box3d"])
+def test_rfm_assembly_matches_generator(csls, case):
+    from workloads import poisson3d
+    p = {"cfg1": lambda: config_problem("cfg1"),
+         "ragged2d": lambda: poisson2d(3, 2, 37, 11, 9, R=1.5, seed=7),
+         "box3d": lambda: poisson3d(2, 3, 2, 24, 5, e_bc=4, e_if=3, R=1.0, seed=9)}[case]()
+    A = _assemble_on_device(csls, p)
+    assert (A.m, A.n, A.nnz) == (p.m, p.n, p.nnz)
+    assert np.array_equal(A.row_ptr.cpu().numpy(), p.row_ptr)
+    assert np.array_equal(A.col.cpu().numpy(), p.col)
+    v = A.val.cpu().numpy()
+    assert np.all(np.abs(v - p.val) <= 1e-13 * np.maximum(1.0, np.abs(p.val)))
+    # the device-assembled matrix gives the same least-squares solution
+    b = torch.tensor(p.b[0], device="cuda")
+    x1, _ = csls.csls_solve(csls.csls_factor(A, seed=3), A, b)
+    Ah = dev(csls, p)
+    x2, _ = csls.csls_solve(csls.csls_factor(Ah, seed=3), Ah, b)
+    Ad = p.dense()
+    assert _anorm_rel(Ad, x1.cpu().numpy(), x2.cpu().numpy()) <= 1e-9
+
+
+def test_rfm_assembly_argument_errors(csls):
+    p = config_problem("cfg1")
+    from workloads import rfm_row_descriptors
+    rows = torch.from_numpy(rfm_row_descriptors(p).view(np.uint8).copy()).cuda()
+    k = torch.tensor(p.k, device="cuda")
+    c = torch.tensor(p.c, device="cuda")
+    with pytest.raises(csls.CslsError):
+        csls.csls_rfm_assemble(2, [0.25, -1.0], p.J, k, c, rows)

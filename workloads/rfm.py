@@ -222,6 +222,60 @@ def _assemble(grid, J, q, e_bc, e_if, R, seed, modes):
                       info=dict(q=q, e_bc=e_bc, e_if=e_if, seed=seed))
 
 
+# One row of the RFM system, as read by the GPU assembly (csls_rfm_assemble): kind 0 = PDE row
+# (-Laplacian at local point t of `box`), 1 = boundary value, 2 = C0 jump and 3 = normal-derivative C1
+# jump across the `axis` face between `box` (local t, t[axis] = +1) and `nbox` (same t with t[axis] = -1).
+RFM_ROW_DTYPE = np.dtype([("kind", np.int32), ("box", np.int32), ("nbox", np.int32), ("axis", np.int32),
+                          ("t", np.float64, (3,))], align=True)
+
+
+def rfm_row_descriptors(p):
+    """Row descriptors of an RFM problem built by poisson2d / poisson3d, in the row order of its CSR."""
+    dim, grid, J = p.dim, tuple(p.grid), p.J
+    q, e_bc, e_if = p.info["q"], p.info["e_bc"], p.info["e_if"]
+    n_boxes = int(np.prod(grid))
+    boxes = [tuple(int(v) for v in np.unravel_index(b, grid[::-1])[::-1]) for b in range(n_boxes)]
+
+    def local_points(qq, fixed=None):
+        t1 = _cell_centres(qq)
+        axes = [t1] * dim
+        if fixed is not None:
+            axis, value = fixed
+            axes[axis] = np.array([value])
+        mesh = np.meshgrid(*axes[::-1], indexing="ij")
+        return np.stack([m.reshape(-1) for m in mesh[::-1]], axis=1)
+
+    parts = []
+
+    def emit(kind, box, nbox, axis, t):
+        rows = np.zeros(t.shape[0], dtype=RFM_ROW_DTYPE)
+        rows["kind"], rows["box"], rows["nbox"], rows["axis"] = kind, box, nbox, axis
+        rows["t"][:, :dim] = t
+        parts.append(rows)
+
+    t_in = local_points(q)
+    for box in range(n_boxes):
+        emit(0, box, -1, -1, t_in)
+    for axis in range(dim):
+        for side, tval in ((0, -1.0), (1, 1.0)):
+            t = local_points(e_bc, fixed=(axis, tval))
+            for box in range(n_boxes):
+                if boxes[box][axis] != (0 if side == 0 else grid[axis] - 1):
+                    continue
+                emit(1, box, -1, axis, t)
+    for order in (0, 1):
+        for axis in range(dim):
+            t_lo = local_points(e_if, fixed=(axis, 1.0))
+            for box in range(n_boxes):
+                idx = boxes[box]
+                if idx[axis] == grid[axis] - 1:
+                    continue
+                nb_idx = list(idx)
+                nb_idx[axis] += 1
+                emit(2 + order, box, _box_index(nb_idx, grid), axis, t_lo)
+    return np.concatenate(parts)
+
+
 def poisson2d(nx, ny, J, q, e=None, R=1.0, seed=1, modes=((1, 1),)):
     """2D Poisson -Laplace u = f on [0,1]^2, u = sin(a pi x) sin(b pi y) for each mode (a, b).
 
