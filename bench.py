@@ -498,14 +498,14 @@ def main():
         traffic = None
         if top == 2:
             # DRAM bytes per average launch: the ncu capture of one k_emu_update launch (2D RFM 6x6
-            # boxes, L=25,600 x n'=3,968) read+wrote 1.697 GB for 1.637 GB of algorithmic bytes (C in
-            # int64 read and written, digit planes); traffic scales with L n', so the average launch
-            # here moves 1.0367 x its algorithmic 16 L n' bytes (sum of L n' = flops / 64)
-            traffic = 1.0367 * (kern_flop[2] / 4.0) / max(kern_n[2], 1)
+            # boxes, L=25,600 x n'=3,936, 64-column outer block) read+wrote 1.624 GB for 1.612 GB of C
+            # traffic (int64, read and written); traffic scales with L n', so the average launch here
+            # moves 1.007 x its algorithmic 16 L n' bytes (sum of L n' = flops / 128)
+            traffic = 1.007 * (kern_flop[2] / 8.0) / max(kern_n[2], 1)
         roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on a smaller "
-                                      "case, scaled per unit (profiles/emu_update_rfm6x6.md)" if traffic else None,
+                                      "case, scaled per unit (profiles/emu_update64_rfm6x6.md)" if traffic else None,
                     "peak_source": src + " bf16 sustained (kernel timed inside a multi-second step)",
                     "fp64_equivalent_tflops": kern_flop[top] / top_s / 1e12, "launches": kern_n[top],
                     "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}

@@ -80,7 +80,8 @@ typedef struct {
     uint64_t seed;        /* count-sketch hash seed */
     int variant;          /* CSLS_VARIANT_QR or CSLS_VARIANT_SVD */
     int factor_prec;      /* CSLS_PREC_F64, CSLS_PREC_F32 or CSLS_PREC_F64_EMU */
-    double rcond;         /* SVD truncation sigma_i > rcond sigma_1; <= 0 means max(s, n) * 2^-53 */
+    double rcond;         /* SVD truncation sigma_i > rcond sigma_1; <= 0 means max(s, n) * 2^-53
+                             (max(s, n) * 2^-38 with CSLS_PREC_F64_EMU) */
     double atol, btol;    /* Paige-Saunders stopping tolerances */
     int64_t maxit;        /* <= 0 means n (Section 4.1) */
     int64_t fixed_iters;  /* > 0: run exactly this many LSQR iterations, no stopping test */

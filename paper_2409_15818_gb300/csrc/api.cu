@@ -523,7 +523,11 @@ static int factor_impl(const csls_csr* A, const double* b, double* x0, const csl
     launches += 3;
     int64_t r = n;
     if (o->variant == CSLS_VARIANT_SVD) {
-        const double rc = o->rcond > 0 ? o->rcond : (double)std::max(s, n) * 1.1102230246251565e-16;
+        // default RCOND = max(s, n) x the unit roundoff of the factorisation: 2^-53 for binary64, 2^-38 for
+        // the emulated products (their relative error per product), so that the noise the emulation leaves
+        // in numerically zero singular values is truncated
+        const double eps = o->factor_prec == CSLS_PREC_F64_EMU ? 3.637978807091713e-12 : 1.1102230246251565e-16;
+        const double rc = o->rcond > 0 ? o->rcond : (double)std::max(s, n) * eps;
         CSLS_TRY(svd_precond((const double*)fp.R, n, rc, ft.G, ft.V, fp.sigma, fp.P, ft.order, &r, ft.err, st,
                              &launches));
     }

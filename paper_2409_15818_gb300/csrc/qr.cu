@@ -171,13 +171,24 @@ k_panel(T* A, int64_t lda, int64_t s, int64_t j0, int nbw, int64_t chunk, T* tau
             for (int r = tid; r < nloc; r += kPanelThreads) A[(r0 + r) + (j0 + c) * lda] = W[c * ld + r];
     }
     if (!grid_sync(bar, G, spin, err)) return;
+    // reduce the Gram partials across the grid: each warp of each CTA owns entries of V^T V and
+    // sums their G partials with its 32 lanes in a fixed order; one more barrier, then CTA 0 forms T
+    T* gram_red = part_gram + (int64_t)G * kPanel * kPanel;   // kPanel^2
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int e = g + warp * G; e < kPanel * kPanel; e += G * (kPanelThreads / 32)) {
+            const int a = e % kPanel, b = e / kPanel;
+            T t = T(0);
+            if (a < nbw && b < nbw && a <= b)
+                for (int q = lane; q < G; q += 32) t += __ldcg(part_gram + (int64_t)q * kPanel * kPanel + e);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) gram_red[e] = t;
+        }
+    }
+    if (!grid_sync(bar, G, spin, err)) return;
     if (g != 0) return;
     for (int p = tid; p < kPanel * kPanel; p += kPanelThreads) {
-        const int a = p % kPanel, b = p / kPanel;
-        T t = T(0);
-        if (a < nbw && b < nbw && a <= b)
-            for (int q = 0; q < G; ++q) t += part_gram[(int64_t)q * kPanel * kPanel + a + b * kPanel];
-        gram[p] = t;
+        gram[p] = __ldcg(gram_red + p);
         tl[p] = T(0);
     }
     __syncthreads();
@@ -561,7 +572,7 @@ QrScratch qr_scratch_carve(Carve& c, int64_t s, int64_t n, int elem_bytes) {
     const size_t e = elem_bytes == 8 ? 1 : 2;   // carve in doubles; floats use half
     q.tau = c.take<double>((size_t)n / e + 1);
     q.T = c.take<double>(kPanel * kPanel);
-    q.part_elems = (int64_t)device_sm_count() * kPartStride + 8;
+    q.part_elems = (int64_t)device_sm_count() * kPartStride + 8 + kPanel * kPanel;
     q.partials = c.take<double>((size_t)q.part_elems);
     q.wp_elems = wp_capacity(n);
     q.Wp = c.take<double>((size_t)q.wp_elems);

@@ -420,16 +420,16 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, 
         else cp_async_commit();                                // keep the group count uniform
         cp_async_wait<1>();
         __syncthreads();
-        // cut this step's C entries into digits (each thread: one column, 4 rows)
-        {
-            const int c = tid >> 3, kq = (tid & 7) * 4;
+        // cut this step's C entries into digits: a warp takes the 32 rows of one column at a time, so
+        // its int64 reads from shared memory are consecutive words (no bank conflicts)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                int d[kDig];
-                digits_fix(sm.Craw[stage][c][kq + e], d);
+        for (int e = 0; e < (kVtcCols * kVtcStep) / kEmuThreads; ++e) {
+            const int idx = e * kEmuThreads + tid;
+            const int c = idx / kVtcStep, k = idx % kVtcStep;
+            int d[kDig];
+            digits_fix(sm.Craw[stage][c][k], d);
 #pragma unroll
-                for (int q = 0; q < kDig; ++q) sm.Bs[q][c][kq + e] = bf16_of_int(d[q]);
-            }
+            for (int q = 0; q < kDig; ++q) sm.Bs[q][c][k] = bf16_of_int(d[q]);
         }
         __syncthreads();
 #pragma unroll

@@ -29,20 +29,21 @@ def csls():
     return mod
 
 
-def _solve(csls, p, seed):
+def _solve(csls, p, seed, prec="f64"):
     A = csls.Csr.from_numpy(p.row_ptr, p.col, p.val, p.m, p.n)
-    F = csls.csls_factor(A, seed=seed, variant="svd")
+    F = csls.csls_factor(A, seed=seed, variant="svd", prec=prec)
     x, rep = csls.csls_solve(F, A, torch.tensor(p.b[0], device="cuda"), variant="svd", tol=1e-14, maxit=500)
     return F, x.cpu().numpy(), rep
 
 
-@pytest.mark.parametrize("name", SMALL + LARGER)
-def test_cssvdp_recovers_rank_and_min_norm_solution(csls, name):
+@pytest.mark.parametrize("name,prec", [(nm, "f64") for nm in SMALL + LARGER] +
+                         [("rel6", "f64emu"), ("ch8-8-b2", "f64emu")])
+def test_cssvdp_recovers_rank_and_min_norm_solution(csls, name, prec):
     p = table_c1_problem(name)
     Ad = p.dense()
     rank = np.linalg.matrix_rank(Ad)
     assert rank == p.info["rank"]
-    F, x, rep = _solve(csls, p, seed=3)
+    F, x, rep = _solve(csls, p, seed=3, prec=prec)
     assert rep["status"] == 0 and rep["istop"] in (1, 2)
     assert rep["r"] == rank
     assert rep["cond_est"] < 10
@@ -50,10 +51,12 @@ def test_cssvdp_recovers_rank_and_min_norm_solution(csls, name):
     x_mn = np.linalg.lstsq(Ad, b, rcond=None)[0]
     assert np.linalg.norm(Ad @ x - b) <= 1e-11 * np.linalg.norm(b)
     # x lies in the row space (P = V_r Sigma_r^-1): it is the minimum-norm solution, determined to
-    # ~cond_r(A) u with cond_r = sigma_1 / sigma_r ~ 1e5..1e6 here
+    # ~cond_r(A) u with cond_r = sigma_1 / sigma_r ~ 1e5..1e6 here and u the factorisation's unit
+    # roundoff (2^-53, or 2^-38 for the emulated products: their error tilts span(V_r) by ~u cond_r)
     sv = np.linalg.svd(Ad, compute_uv=False)
     kappa_r = sv[0] / sv[rank - 1]
-    assert np.linalg.norm(x - x_mn) <= max(1e-10, 50 * kappa_r * 2.0 ** -53) * np.linalg.norm(x_mn)
+    u = 2.0 ** -53 if prec == "f64" else 2.0 ** -38
+    assert np.linalg.norm(x - x_mn) <= max(1e-10, 50 * kappa_r * u) * np.linalg.norm(x_mn)
 
 
 @pytest.mark.parametrize("name", SMALL)
