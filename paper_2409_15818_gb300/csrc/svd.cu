@@ -14,7 +14,8 @@ namespace csls {
 constexpr int kJacThreads = 256;
 
 __global__ void __launch_bounds__(kJacThreads)
-k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double tol, unsigned* rotations) {
+k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double tol, double floor_c,
+              unsigned* rotations) {
     __shared__ double red[3][kJacThreads / 32];
     __shared__ double cs_s[2];
     __shared__ int skip_s;
@@ -48,7 +49,10 @@ k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double t
     if (threadIdx.x == 0) {
         double A = 0.0, B = 0.0, C = 0.0;
         for (int w = 0; w < kJacThreads / 32; ++w) { A += red[0][w]; B += red[1][w]; C += red[2][w]; }
-        if (C == 0.0 || fabs(C) <= tol * sqrt(A * B)) {
+        // no rotation when the pair is already orthogonal to working accuracy, or when its inner
+        // product is below the rounding floor of the whole matrix (pairs of numerically zero columns
+        // of a rank-deficient R would otherwise keep rotating on noise)
+        if (C == 0.0 || fabs(C) <= tol * sqrt(A * B) || fabs(C) <= floor_c) {
             skip_s = 1;
         } else {
             skip_s = 0;
@@ -118,11 +122,21 @@ int svd_precond(const double* R, int64_t n, double rcond, double* G, double* V, 
     // rotations counter lives in the first word of `order` until the ordering is written
     unsigned* rot = reinterpret_cast<unsigned*>(order);
     const double tol = 1e-15;
+    // rounding floor of the inner products: n u^2 ||R||_F^2 (P is scratch until it is formed)
+    k_col_norms<<<(unsigned)n, kJacThreads, 0, st>>>(G, n, P);
+    CSLS_CUDA(cudaGetLastError());
+    std::vector<double> cn((size_t)n);
+    CSLS_CUDA(cudaMemcpyAsync(cn.data(), P, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CSLS_CUDA(cudaStreamSynchronize(st));
+    double frob2 = 0.0;
+    for (double v : cn) frob2 += v * v;
+    const double u = 1.1102230246251565e-16;
+    const double floor_c = (double)n * u * u * frob2;
     int64_t nl = 1;
     for (int sweep = 0; sweep < 60 && N >= 2; ++sweep) {
         CSLS_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned), st));
         for (int64_t step = 0; step < N - 1; ++step) {
-            k_jacobi_step<<<(unsigned)(N / 2), kJacThreads, 0, st>>>(G, V, n, N, step, tol, rot);
+            k_jacobi_step<<<(unsigned)(N / 2), kJacThreads, 0, st>>>(G, V, n, N, step, tol, floor_c, rot);
             CSLS_CUDA(cudaGetLastError());
         }
         nl += N - 1;
