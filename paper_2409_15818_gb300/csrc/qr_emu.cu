@@ -479,30 +479,34 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, 
 
 // ------------------------------------------------------------------ C += V Wn  (exact integer update)
 
-constexpr int kUpdRows = 64, kUpdCols = 64, kUpdPad = 8, kUpdLdk = kOB + kUpdPad;   // 72
+constexpr int kUpdRows = 64, kUpdPad = 8, kUpdLdk = kOB + kUpdPad;   // 72
 
+template <int UC>
 struct UpdSmem {
     unsigned short Vs[kDig][kUpdRows][kUpdLdk];   // [p][r][a]
-    unsigned short Ws[kDig][kUpdCols][kUpdLdk];   // [q][c][a]
+    unsigned short Ws[kDig][UC][kUpdLdk];         // [q][c][a]
     int frow[kUpdRows];
-    int gcol[kUpdCols];
-    int ecol[kUpdCols];
+    int gcol[UC];
+    int ecol[UC];
 };
 
-// KM: products over the first KM digit columns (64, or 32 when the outer block has one panel).
-template <int KM>
-__global__ void __launch_bounds__(kEmuThreads, 2)
+// C tile of 64 rows x UC columns; 8 warps as 2 (rows) x 4 (columns), each warp 32 rows x UC/4 columns
+// (NT n8 tiles). KM: products over the first KM digit columns (64, or 32 when the outer block has
+// one panel). MB: CTAs per SM the register budget is sized for.
+template <int KM, int UC, int MB>
+__global__ void __launch_bounds__(kEmuThreads, MB)
 k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int nbo, const unsigned short* Vd,
              int64_t ldv, const int* frow, const unsigned short* Wd, int64_t ldw, const int* gcol, const int* E,
              int64_t nprime) {
+    constexpr int NT = UC / 32;   // n8 tiles per warp
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    UpdSmem& sm = *reinterpret_cast<UpdSmem*>(smem_raw);
+    UpdSmem<UC>& sm = *reinterpret_cast<UpdSmem<UC>*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
     const int64_t jc = J0 + nbo;
     const int64_t L = s - J0;
     const int64_t rb = (int64_t)blockIdx.x * kUpdRows;   // local row of tile row 0
-    const int64_t cb = (int64_t)blockIdx.y * kUpdCols;   // trailing column of tile col 0
-    const int wm = warp & 1, wn = warp >> 1;             // warp tile: rows wm*32..+32, cols wn*16..+16
+    const int64_t cb = (int64_t)blockIdx.y * UC;         // trailing column of tile col 0
+    const int wm = warp & 1, wn = warp >> 1;             // warp tile: rows wm*32..+32, cols wn*(UC/4)..
     // digit tiles: each row of 64 bf16 is 8 chunks of 16 B
     for (int idx = tid; idx < kDig * kUpdRows * 8; idx += kEmuThreads) {
         const int ch = idx & 7, r = (idx >> 3) % kUpdRows, p = (idx >> 3) / kUpdRows;
@@ -510,8 +514,8 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int
         const bool ok = lr < L;
         cp_async16(&sm.Vs[p][r][ch * 8], Vd + ((int64_t)p * ldv + (ok ? lr : 0)) * kOB + ch * 8, ok ? 16 : 0);
     }
-    for (int idx = tid; idx < kDig * kUpdCols * 8; idx += kEmuThreads) {
-        const int ch = idx & 7, c = (idx >> 3) % kUpdCols, q = (idx >> 3) / kUpdCols;
+    for (int idx = tid; idx < kDig * UC * 8; idx += kEmuThreads) {
+        const int ch = idx & 7, c = (idx >> 3) % UC, q = (idx >> 3) / UC;
         const int64_t col = cb + c;
         const bool ok = col < nprime;
         cp_async16(&sm.Ws[q][c][ch * 8], Wd + ((int64_t)q * ldw + (ok ? col : 0)) * kOB + ch * 8, ok ? 16 : 0);
@@ -519,55 +523,61 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int
     cp_async_commit();
     // this warp's C entries are loaded while the digit tiles are in flight; they are only
     // needed after the products
-    long long cval[2][2][4];
+    long long cval[2][NT][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const int64_t lr = rb + wm * 32 + i * 16 + g + (h >> 1) * 8;
-                const int64_t col = cb + wn * 16 + j * 8 + 2 * t + (h & 1);
+                const int64_t col = cb + wn * (UC / 4) + j * 8 + 2 * t + (h & 1);
                 cval[i][j][h] = (lr < L && col < nprime) ? Cfix[(J0 + lr) + (jc + col) * lda] : 0LL;
             }
     for (int i = tid; i < kUpdRows; i += kEmuThreads) sm.frow[i] = rb + i < L ? frow[rb + i] : 0;
-    for (int i = tid; i < kUpdCols; i += kEmuThreads) {
+    for (int i = tid; i < UC; i += kEmuThreads) {
         sm.gcol[i] = cb + i < nprime ? gcol[cb + i] : 0;
         sm.ecol[i] = cb + i < nprime ? E[jc + cb + i] : 0;
     }
     cp_async_wait<0>();
     __syncthreads();
-    long long acc64[2][2][4];
+    long long acc64[2][NT][4];
 #pragma unroll 1
     for (int l = 0; l <= kLev; ++l) {
-        float acc[2][2][4];
+        float acc[2][NT][4];
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < NT; ++j)
 #pragma unroll
                 for (int h = 0; h < 4; ++h) acc[i][j][h] = 0.0f;
         for (int p = 0; p <= l; ++p) {
             const int q = l - p;
 #pragma unroll
             for (int ks = 0; ks < KM; ks += 16) {
-                uint32_t af[2][4], bq[4];
+                uint32_t af[2][4], bq[NT / 2][4];
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
                     ldsm_x4(af[i], &sm.Vs[p][wm * 32 + i * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
-                ldsm_x4(bq, &sm.Ws[q][wn * 16 + (lane & 7) + ((lane >> 4) & 1) * 8][ks + ((lane >> 3) & 1) * 8]);
-                const uint32_t bfr[2][2] = {{bq[0], bq[1]}, {bq[2], bq[3]}};
+#pragma unroll
+                for (int jj = 0; jj < NT / 2; ++jj)
+                    ldsm_x4(bq[jj], &sm.Ws[q][wn * (UC / 4) + jj * 16 + (lane & 7) + ((lane >> 4) & 1) * 8]
+                                         [ks + ((lane >> 3) & 1) * 8]);
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) hmma(acc[i][j], af[i], bfr[j]);
+                    for (int jj = 0; jj < NT / 2; ++jj) {
+                        const uint32_t b0[2] = {bq[jj][0], bq[jj][1]}, b1[2] = {bq[jj][2], bq[jj][3]};
+                        hmma(acc[i][2 * jj], af[i], b0);
+                        hmma(acc[i][2 * jj + 1], af[i], b1);
+                    }
             }
         }
         // every level sum is an integer below 6 x 64 x 2^14 < 2^24: exact in FP32
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < NT; ++j)
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const long long v = (long long)__float2int_rn(acc[i][j][h]);
@@ -578,11 +588,11 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const int r = wm * 32 + i * 16 + g + (h >> 1) * 8;
-                const int c = wn * 16 + j * 8 + 2 * t + (h & 1);
+                const int c = wn * (UC / 4) + j * 8 + 2 * t + (h & 1);
                 const int64_t lr = rb + r, col = cb + c;
                 if (lr < L && col < nprime) {
                     const int sh = sm.frow[r] + sm.gcol[c] - 14 - 8 * kLev + kFixBits - sm.ecol[c];
@@ -595,6 +605,11 @@ k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int
                 }
             }
 }
+
+// Tile width of the update: 64 columns, 2 CTAs per SM (measured faster than 128 columns with one CTA
+// per SM and 32 x 32 warp tiles: 0.75 s against 0.70 s per factor on the 2D bench workload).
+constexpr int kUpdCols = 64;
+constexpr int kUpdMinBlocks = kUpdCols == 64 ? 2 : 1;
 
 // ------------------------------------------------------------------ scratch and driver
 
@@ -662,10 +677,10 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     static bool attr = false;
     if (!attr) {
         CSLS_CUDA(cudaFuncSetAttribute(k_emu_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(VtcSmem)));
-        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kOB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(UpdSmem)));
-        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kPanel>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(UpdSmem)));
+        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kOB, kUpdCols, kUpdMinBlocks>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpdSmem<kUpdCols>)));
+        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kPanel, kUpdCols, kUpdMinBlocks>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpdSmem<kUpdCols>)));
         CSLS_CUDA(cudaFuncSetAttribute(k_wreduce_ob, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWrSmem));
         attr = true;
     }
@@ -754,14 +769,15 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         CSLS_CUDA(cudaGetLastError());
         tk = kt_begin(kFamUpdate, st);
         const dim3 ug((unsigned)ceil_div(L, kUpdRows), (unsigned)ceil_div(nprime, kUpdCols));
+        const size_t usm = sizeof(UpdSmem<kUpdCols>);
         if (nbo > kPanel)   // zero digits past nbo need no products
-            k_emu_update<kOB><<<ug, kEmuThreads, sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n, J0,
-                                                                        nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp, e.gcol,
-                                                                        e.E, nprime);
+            k_emu_update<kOB, kUpdCols, kUpdMinBlocks><<<ug, kEmuThreads, usm, st>>>(
+                reinterpret_cast<long long*>(A), lda, s, n, J0, nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp, e.gcol, e.E,
+                nprime);
         else
-            k_emu_update<kPanel><<<ug, kEmuThreads, sizeof(UpdSmem), st>>>(reinterpret_cast<long long*>(A), lda, s, n,
-                                                                           J0, nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp,
-                                                                           e.gcol, e.E, nprime);
+            k_emu_update<kPanel, kUpdCols, kUpdMinBlocks><<<ug, kEmuThreads, usm, st>>>(
+                reinterpret_cast<long long*>(A), lda, s, n, J0, nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp, e.gcol, e.E,
+                nprime);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
         nl += 7;
