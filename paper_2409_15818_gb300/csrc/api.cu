@@ -528,8 +528,8 @@ static int factor_impl(const csls_csr* A, const double* b, double* x0, const csl
         // in numerically zero singular values is truncated
         const double eps = o->factor_prec == CSLS_PREC_F64_EMU ? 3.637978807091713e-12 : 1.1102230246251565e-16;
         const double rc = o->rcond > 0 ? o->rcond : (double)std::max(s, n) * eps;
-        CSLS_TRY(svd_precond((const double*)fp.R, n, rc, ft.G, ft.V, fp.sigma, fp.P, ft.order, &r, ft.err, st,
-                             &launches));
+        CSLS_TRY(svd_precond((const double*)fp.R, n, rc, ft.G, ft.V, fp.sigma, fp.P, ft.order, &r, ft.qr.bar, spin,
+                             ft.err, st, &launches));
     }
     const double ms_qr = t_qr.stop();
     kts.collect(rep);

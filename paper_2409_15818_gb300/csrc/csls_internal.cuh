@@ -215,7 +215,8 @@ int diag_block_inverses_f32(const float* R, int64_t n, double* Dinv, cudaStream_
 
 // Jacobi SVD of R (n x n): sigma (desc), V (n x n), P = V_r Sigma_r^{-1}; returns r in *r_out (host).
 int svd_precond(const double* R, int64_t n, double rcond, double* work_G, double* work_V, double* sigma,
-                double* P, int* order, int64_t* r_out, int* err, cudaStream_t st, int64_t* launches);
+                double* P, int* order, int64_t* r_out, GridBarrier* bar, long long spin, int* err, cudaStream_t st,
+                int64_t* launches);
 
 }  // namespace csls
 

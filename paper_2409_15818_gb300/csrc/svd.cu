@@ -13,13 +13,11 @@ namespace csls {
 
 constexpr int kJacThreads = 256;
 
-__global__ void __launch_bounds__(kJacThreads)
-k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double tol, double floor_c,
-              unsigned* rotations) {
-    __shared__ double red[3][kJacThreads / 32];
-    __shared__ double cs_s[2];
-    __shared__ int skip_s;
-    const int64_t pidx = blockIdx.x;   // pair index in [0, N/2)
+// One plane rotation of the column pair with index pidx in round-robin step `step` (all threads
+// of the CTA take part; shared scratch is passed in).
+__device__ __forceinline__ void jacobi_pair(double* G, double* V, int64_t n, int64_t N, int64_t step, int64_t pidx,
+                                            double tol, double floor_c, unsigned* rotations, double (*red)[kJacThreads / 32],
+                                            double* cs_s, int* skip_s) {
     int64_t a, b;
     if (pidx == 0) {
         a = step % (N - 1);
@@ -29,7 +27,7 @@ k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double t
         b = (step - pidx + (N - 1)) % (N - 1);
     }
     if (a > b) { int64_t t = a; a = b; b = t; }
-    if (b >= n) return;   // padding column
+    if (b >= n) return;   // padding column (uniform across the CTA)
     double* ga = G + a * n;
     double* gb = G + b * n;
     double saa = 0.0, sbb = 0.0, sab = 0.0;
@@ -53,9 +51,9 @@ k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double t
         // product is below the rounding floor of the whole matrix (pairs of numerically zero columns
         // of a rank-deficient R would otherwise keep rotating on noise)
         if (C == 0.0 || fabs(C) <= tol * sqrt(A * B) || fabs(C) <= floor_c) {
-            skip_s = 1;
+            *skip_s = 1;
         } else {
-            skip_s = 0;
+            *skip_s = 0;
             const double zeta = (B - A) / (2.0 * C);
             const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double c = 1.0 / sqrt(1.0 + t * t);
@@ -65,8 +63,10 @@ k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double t
         }
     }
     __syncthreads();
-    if (skip_s) return;
+    const int skip = *skip_s;
     const double c = cs_s[0], s = cs_s[1];
+    __syncthreads();   // the shared scratch is reused by the CTA's next pair
+    if (skip) return;
     double* va = V + a * n;
     double* vb = V + b * n;
     for (int64_t i = threadIdx.x; i < n; i += kJacThreads) {
@@ -76,6 +76,21 @@ k_jacobi_step(double* G, double* V, int64_t n, int64_t N, int64_t step, double t
         const double p = va[i], q = vb[i];
         va[i] = c * p - s * q;
         vb[i] = s * p + c * q;
+    }
+}
+
+// A whole sweep in one cooperative launch: the N - 1 round-robin steps are separated by grid
+// barriers; a CTA takes pairs blockIdx.x, blockIdx.x + gridDim.x, ... of each step.
+__global__ void __launch_bounds__(kJacThreads)
+k_jacobi_sweep(double* G, double* V, int64_t n, int64_t N, double tol, double floor_c, unsigned* rotations,
+               GridBarrier* bar, long long spin, int* err) {
+    __shared__ double red[3][kJacThreads / 32];
+    __shared__ double cs_s[2];
+    __shared__ int skip_s;
+    for (int64_t step = 0; step < N - 1; ++step) {
+        for (int64_t pidx = blockIdx.x; pidx < N / 2; pidx += gridDim.x)
+            jacobi_pair(G, V, n, N, step, pidx, tol, floor_c, rotations, red, cs_s, &skip_s);
+        if (!grid_sync(bar, gridDim.x, spin, err)) return;
     }
 }
 
@@ -114,8 +129,7 @@ __global__ void k_form_p(const double* V, const double* sigma, const int* order,
 }
 
 int svd_precond(const double* R, int64_t n, double rcond, double* G, double* V, double* sigma, double* P, int* order,
-                int64_t* r_out, int* err, cudaStream_t st, int64_t* launches) {
-    (void)err;
+                int64_t* r_out, GridBarrier* bar, long long spin, int* err, cudaStream_t st, int64_t* launches) {
     const int64_t N = n + (n & 1);
     k_copy_init<<<(unsigned)std::min<int64_t>(ceil_div(n * n, 256), 65535), 256, 0, st>>>(R, G, V, n);
     CSLS_CUDA(cudaGetLastError());
@@ -130,19 +144,29 @@ int svd_precond(const double* R, int64_t n, double rcond, double* G, double* V, 
     CSLS_CUDA(cudaStreamSynchronize(st));
     double frob2 = 0.0;
     for (double v : cn) frob2 += v * v;
+    // below (1e-2 rcond)^2 ||R||_F^2 an inner product is noise of columns that end up truncated, or turns
+    // a column at the truncation edge by less than 1e-4 rad: such pairs are left alone, so the sweeps of a
+    // rank-deficient R converge instead of rotating its numerically zero columns on rounding noise
     const double u = 1.1102230246251565e-16;
-    const double floor_c = (double)n * u * u * frob2;
+    const double floor_c = std::max((double)n * u * u, 1e-4 * rcond * rcond) * frob2;
     int64_t nl = 1;
+    int per_sm = 0;
+    CSLS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_sweep, kJacThreads, 0));
+    const int64_t resident = (int64_t)std::max(per_sm, 1) * device_sm_count();
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(N / 2, resident));
+    CSLS_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
     for (int sweep = 0; sweep < 60 && N >= 2; ++sweep) {
         CSLS_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned), st));
-        for (int64_t step = 0; step < N - 1; ++step) {
-            k_jacobi_step<<<(unsigned)(N / 2), kJacThreads, 0, st>>>(G, V, n, N, step, tol, floor_c, rot);
-            CSLS_CUDA(cudaGetLastError());
-        }
-        nl += N - 1;
+        void* args[] = {&G, (void*)&V, (void*)&n, (void*)&N, (void*)&tol, (void*)&floor_c, (void*)&rot, (void*)&bar,
+                        (void*)&spin, (void*)&err};
+        CSLS_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_sweep, dim3(grid), dim3(kJacThreads), args, 0, st));
+        nl += 1;
         unsigned h_rot = 0;
+        int h_err = 0;
         CSLS_CUDA(cudaMemcpyAsync(&h_rot, rot, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CSLS_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CSLS_CUDA(cudaStreamSynchronize(st));
+        if (h_err) return CSLS_OK;   // the caller reads the error word
         if (h_rot == 0) break;
     }
     // sigma_j = ||G_j||, sorted descending on the host (n values)

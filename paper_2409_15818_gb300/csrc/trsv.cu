@@ -67,6 +67,7 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     // entries are still to be fetched, so the chain from block to block carries no R traffic.
     const double* D = Dinv + (int64_t)b * kTs * kTs;
     for (int i = tid; i < kTs * kTs; i += kTsThreads) dsm[i] = __ldg(D + i);
+    const double vpre = (tid < bs) ? v[r0 + tid] * coef[0] : 0.0;   // this block's right-hand side
     double rv[16];
     auto load_block = [&](int c, double (&dst)[16]) {
         const int64_t c0 = (int64_t)c * kTs;
@@ -99,7 +100,7 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     __syncthreads();
     if (tid < kTs) {
         double r = 0.0;
-        if (tid < bs) r = v[r0 + tid] * coef[0] - (((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid]);
+        if (tid < bs) r = vpre - (((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid]);
         rhs[tid] = r;
     }
     __syncthreads();
@@ -111,15 +112,17 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     }
     part[q][row] = a2;
     __syncthreads();
+    double zb = 0.0;
     if (tid < bs) {
-        const double zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
+        zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
         z[r0 + tid] = zb;
-        if (MODE == 1) xw_update(st, coef[3] != 0.0, coef[1], coef[2], zb, wx, x, r0 + tid);
     }
     __threadfence();
     __syncthreads();
+    // publish this block first: the x / w epilogue below touches only this block's rows
+    if (tid == 0) st_release(&flags[b], want);
+    if (MODE == 1 && tid < bs) xw_update(st, coef[3] != 0.0, coef[1], coef[2], zb, wx, x, r0 + tid);
     if (tid == 0) {
-        st_release(&flags[b], want);
         unsigned prev = atomicAdd(&ctl->done, 1u);
         if (prev == (unsigned)nb - 1) {
             ctl->ticket = 0;
@@ -164,6 +167,9 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     // the flag that releases them
     const double* D = Dinv + (int64_t)b * kTs * kTs;
     for (int i = tid; i < kTs * kTs; i += kTsThreads) dsm[i] = __ldg(D + i);
+    // this block's own entries of g and v: read only by this CTA, so they are loaded up front
+    const double gpre = (tid < bs) ? g[r0 + tid] : 0.0;
+    const double vtpre = (MODE == 1 && tid < bs) ? vt[r0 + tid] : 0.0;
     double rv[16];
     auto load_block = [&](int c, double (&dst)[16]) {
         const int64_t c0 = (int64_t)c * kTs;
@@ -194,7 +200,7 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     __syncthreads();
     if (tid < kTs) {
         double r = 0.0;
-        if (tid < bs) r = g[r0 + tid] - (((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid]);
+        if (tid < bs) r = gpre - (((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid]);
         rhs[tid] = r;
     }
     __syncthreads();
@@ -206,14 +212,20 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     }
     part[q][col] = a2;
     __syncthreads();
-    double sq = 0.0;
+    double sq = 0.0, zb = 0.0;
     if (tid < bs) {
-        const double zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
+        zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
         g[r0 + tid] = zb;
+    }
+    __threadfence();
+    __syncthreads();
+    // publish this block first: the epilogue below touches only this block's rows
+    if (tid == 0) st_release(&flags[b], want);
+    if (tid < bs) {
         if (MODE == 0) {
             if (out != g) out[r0 + tid] = zb;
         } else {
-            const double vn = MODE == 1 ? zb - coef[0] * vt[r0 + tid] : zb;
+            const double vn = MODE == 1 ? zb - coef[0] * vtpre : zb;
             vt[r0 + tid] = vn;
             sq = vn * vn;
         }
@@ -231,7 +243,6 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
             partials[b] = t;
             __threadfence();
         }
-        st_release(&flags[b], want);
         unsigned prev = atomicAdd(&ctl->done, 1u);
         if (prev == (unsigned)nb - 1) {
             __threadfence();
