@@ -5,6 +5,7 @@
 // pair, accumulating the same rotations into V. Sweeps repeat until no pair
 // needs a rotation. Then P = V_r Sigma_r^{-1} keeps sigma_i > rcond sigma_1.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "csls_internal.cuh"
@@ -47,10 +48,10 @@ __device__ __forceinline__ void jacobi_pair(double* G, double* V, int64_t n, int
     if (threadIdx.x == 0) {
         double A = 0.0, B = 0.0, C = 0.0;
         for (int w = 0; w < kJacThreads / 32; ++w) { A += red[0][w]; B += red[1][w]; C += red[2][w]; }
-        // no rotation when the pair is already orthogonal to working accuracy, or when its inner
-        // product is below the rounding floor of the whole matrix (pairs of numerically zero columns
-        // of a rank-deficient R would otherwise keep rotating on noise)
-        if (C == 0.0 || fabs(C) <= tol * sqrt(A * B) || fabs(C) <= floor_c) {
+        // no rotation when the pair is already orthogonal to working accuracy, when its inner product
+        // is below the floor, or when one column's squared norm is (that column is truncated later; the
+        // numerically zero columns of a rank-deficient R would otherwise keep rotating on noise)
+        if (C == 0.0 || fabs(C) <= tol * sqrt(A * B) || fabs(C) <= floor_c || fmin(A, B) <= floor_c) {
             *skip_s = 1;
         } else {
             *skip_s = 0;
@@ -135,7 +136,10 @@ int svd_precond(const double* R, int64_t n, double rcond, double* G, double* V, 
     CSLS_CUDA(cudaGetLastError());
     // rotations counter lives in the first word of `order` until the ordering is written
     unsigned* rot = reinterpret_cast<unsigned*>(order);
-    const double tol = 1e-15;
+    // a pair counts as orthogonal once |g_a^T g_b| <= sqrt(n) u ||g_a|| ||g_b|| (the convergence test of
+    // LAPACK's one-sided Jacobi): tighter than the rounding of the dot products themselves, sweeps would
+    // keep rotating pairs on noise
+    const double tol = std::max(1e-15, std::sqrt((double)n) * 1.1102230246251565e-16);
     // rounding floor of the inner products: n u^2 ||R||_F^2 (P is scratch until it is formed)
     k_col_norms<<<(unsigned)n, kJacThreads, 0, st>>>(G, n, P);
     CSLS_CUDA(cudaGetLastError());
