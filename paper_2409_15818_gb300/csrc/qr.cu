@@ -449,6 +449,21 @@ __global__ void __launch_bounds__(256) k_vtc_f32(const float* A, int64_t lda, in
     }
 }
 
+// Wp[0](b, c) = sum_ks Wp[ks](b, c) for every entry (b < nbw), a warp per entry, fixed order.
+template <class T>
+__global__ void __launch_bounds__(256) k_psum(T* Wp, int KS, int nbw, int64_t nprime) {
+    const int lane = threadIdx.x & 31;
+    const int64_t entries = (int64_t)nbw * nprime;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < entries; e += nw) {
+        const int64_t bb = e / nprime, c = e % nprime;
+        T t = T(0);
+        for (int q = lane; q < KS; q += 32) t += Wp[((int64_t)q * kPanel + bb) * nprime + c];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) Wp[bb * nprime + c] = t;
+    }
+}
+
 // Wn(a, c) = -sum_{b <= a} T(b, a) sum_ks Wp[ks](b, c). A CTA owns 32 columns: one thread per
 // (b, c) entry sums its partials (coalesced along c), then one per (a, c) forms -T^T W.
 constexpr int kWrCols = 32;
@@ -595,7 +610,6 @@ static int trailing_update(T* A, int64_t lda, int64_t s, int64_t n, int64_t j0, 
     int64_t ks = ceil_div(4LL * device_sm_count(), ntn);
     const int64_t maxks = ceil_div(L, kVtcRows);
     if (ks > maxks) ks = maxks;
-    if (ks > 64) ks = 64;   // narrow trailing blocks: a few long row chunks keep the partial sums short
     if (ks < 1) ks = 1;
     while (ks > 1 && ks * kPanel * ntn * kVtcN > q.wp_elems * (int64_t)(8 / sizeof(T))) --ks;
     const int64_t kc = round_up(ceil_div(L, ks), kVtcRows);
@@ -610,7 +624,17 @@ static int trailing_update(T* A, int64_t lda, int64_t s, int64_t n, int64_t j0, 
                                                                      (float*)Wp, nprime);
     CSLS_CUDA(cudaGetLastError());
     kt_end(tk, prod_flop, st);
-    k_wreduce<T><<<(unsigned)ceil_div(nprime, kWrCols), 256, 0, st>>>(Wp, (int)ks, Tm, nbw, Wn, nprime);
+    int ksr = (int)ks;
+    if (ks > 8) {
+        // many row chunks (narrow trailing blocks): sum the partials of each entry with a warp first,
+        // in place into chunk 0, so that the T^T product below reads one partial per entry
+        const int64_t entries = (int64_t)nbw * nprime;
+        const int g = (int)std::min<int64_t>(ceil_div(entries * 32, 256), (int64_t)device_sm_count() * 8);
+        k_psum<T><<<g, 256, 0, st>>>(Wp, (int)ks, nbw, nprime);
+        CSLS_CUDA(cudaGetLastError());
+        ksr = 1;
+    }
+    k_wreduce<T><<<(unsigned)ceil_div(nprime, kWrCols), 256, 0, st>>>(Wp, ksr, Tm, nbw, Wn, nprime);
     CSLS_CUDA(cudaGetLastError());
     dim3 ug((unsigned)ceil_div(L, kUpdM), (unsigned)ceil_div(nprime, kUpdN));
     tk = timed ? kt_begin(kFamUpdate, st) : -1;
