@@ -137,6 +137,26 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """The slowest rank's figure (whole-job time is set by the last rank to finish)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_problem(config, rank):
+    """The workload of one replica: independent instances of the same recipe (a different seed per
+    rank for the 2D bench workload), so N ranks solve N independent problems with no exchange."""
+    from workloads import config_problem, poisson2d
+    if config == "cfg2":
+        return poisson2d(8, 8, 200, 30, 30, R=2.0, seed=2 + 1000 * rank)
+    return config_problem(config)
+
+
 def qr_flops(s, n):
     return 2.0 * s * n * n - 2.0 / 3.0 * n ** 3
 
@@ -296,10 +316,7 @@ def main():
     from paper_2409_15818_gb300 import csls
     from workloads import config_problem, poisson2d
 
-    if args.config == "cfg2":
-        p = poisson2d(8, 8, 200, 30, 30, R=2.0, seed=2 + 1000 * rank)   # one instance per replica
-    else:
-        p = config_problem(args.config)
+    p = replica_problem(args.config, rank)   # one instance per replica
     m, n, nnz = p.m, p.n, p.nnz
     s = min(4 * n, m)
     global WORKLOAD
@@ -363,11 +380,7 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / max(args.steps, 1), world)
     status = rep["status"]
 
     # the plain binary64 form (trailing updates on the FP64 MMA pipe), timed once beside the chosen form
@@ -468,11 +481,7 @@ def main():
         h_x.copy_(x2, non_blocking=True)
     q1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = q0.elapsed_time(q1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(q0.elapsed_time(q1) / e2e_steps, world)
 
     # roofline of the dominant kernel: of the factor's three kernel families (Householder panel,
     # W = V^T C, C -= V W), the one with the most device time over the timed steps, its CUDA-event
