@@ -724,12 +724,6 @@ int qr_panel_launch_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, 
     return CSLS_OK;
 }
 
-int qr_wreduce_launch_f64(const QrScratch& q, int ks, int nbw, int64_t nprime, cudaStream_t st) {
-    k_wreduce<double><<<(unsigned)ceil_div(nprime, kWrCols), 256, 0, st>>>(q.Wp, ks, q.T, nbw, q.Wn, nprime);
-    CSLS_CUDA(cudaGetLastError());
-    return CSLS_OK;
-}
-
 int qr_factor_f64(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, int* err, long long spin,
                   cudaStream_t st, int64_t* launches) {
     return qr_factor_impl<double>(A, lda, s, n, q, err, spin, st, launches);
