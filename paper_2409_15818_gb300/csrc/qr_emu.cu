@@ -213,16 +213,30 @@ __global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, i
             if (lr < L) mx = fmax(mx, fabs(vmask(A, lda, r, J0, a)));
         const int f = exp_of(mx);
         frow[lr] = f;
-        for (int a = 0; a < kOB; ++a) {
-            const double v = (lr < L && a < nbo) ? vmask(A, lda, r, J0, a) : 0.0;
-            int d[kDig], dt[kDig];
-            digits_f64(v, f, d);
-            digits_f64(v, ecol_s[a], dt);
+        // the row-scaled digits of 8 consecutive columns go out as one 16-byte store per plane (a
+        // thread owns a row, so its 64 entries of a plane are contiguous); the column-scaled planes are
+        // written entry by entry, consecutive across the threads
+        for (int a0 = 0; a0 < kOB; a0 += 8) {
+            uint32_t pk[kDig][4];
 #pragma unroll
-            for (int p = 0; p < kDig; ++p) {
-                Vd[((int64_t)p * ldv + lr) * kOB + a] = bf16_of_int(d[p]);
-                VTd[((int64_t)p * kOB + a) * ldv + lr] = bf16_of_int(dt[p]);
+            for (int j = 0; j < 8; ++j) {
+                const int a = a0 + j;
+                const double v = (lr < L && a < nbo) ? vmask(A, lda, r, J0, a) : 0.0;
+                int d[kDig], dt[kDig];
+                digits_f64(v, f, d);
+                digits_f64(v, ecol_s[a], dt);
+#pragma unroll
+                for (int p = 0; p < kDig; ++p) {
+                    const uint32_t h = bf16_of_int(d[p]);
+                    if (j & 1) pk[p][j >> 1] |= h << 16;
+                    else pk[p][j >> 1] = h;
+                    VTd[((int64_t)p * kOB + a) * ldv + lr] = bf16_of_int(dt[p]);
+                }
             }
+#pragma unroll
+            for (int p = 0; p < kDig; ++p)
+                *reinterpret_cast<uint4*>(Vd + ((int64_t)p * ldv + lr) * kOB + a0) =
+                    make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
         }
     }
 }
@@ -268,12 +282,25 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
             if (c < nprime) mx = fmax(mx, fabs(Wn[(int64_t)a * nprime + c]));
         const int g = exp_of(mx);
         gcol[c] = g;
-        for (int a = 0; a < kOB; ++a) {
-            const double w = (c < nprime && a < nbo) ? Wn[(int64_t)a * nprime + c] : 0.0;
-            int d[kDig];
-            digits_f64(w, g, d);
+        for (int a0 = 0; a0 < kOB; a0 += 8) {   // 16-byte stores, as in k_vdigits
+            uint32_t pk[kDig][4];
 #pragma unroll
-            for (int p = 0; p < kDig; ++p) Wd[((int64_t)p * ldw + c) * kOB + a] = bf16_of_int(d[p]);
+            for (int j = 0; j < 8; ++j) {
+                const int a = a0 + j;
+                const double w = (c < nprime && a < nbo) ? Wn[(int64_t)a * nprime + c] : 0.0;
+                int d[kDig];
+                digits_f64(w, g, d);
+#pragma unroll
+                for (int p = 0; p < kDig; ++p) {
+                    const uint32_t h = bf16_of_int(d[p]);
+                    if (j & 1) pk[p][j >> 1] |= h << 16;
+                    else pk[p][j >> 1] = h;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < kDig; ++p)
+                *reinterpret_cast<uint4*>(Wd + ((int64_t)p * ldw + c) * kOB + a0) =
+                    make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
         }
     }
 }
