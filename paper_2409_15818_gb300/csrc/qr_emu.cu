@@ -338,6 +338,17 @@ __global__ void __launch_bounds__(256) k_gram12(const double* A, int64_t lda, in
     for (int i = 0; i < 4; ++i) part[(int64_t)blockIdx.x * kPanel * kPanel + a + (4 * bq + i) * kPanel] = acc[i];
 }
 
+// part[0][e] = sum over the nparts partials of entry e (a warp per entry, fixed order).
+__global__ void __launch_bounds__(256) k_gsum(double* part, int nparts) {
+    const int lane = threadIdx.x & 31;
+    const int e = (blockIdx.x * 256 + threadIdx.x) >> 5;
+    if (e >= kPanel * kPanel) return;
+    double t = 0.0;
+    for (int k = lane; k < nparts; k += 32) t += part[(int64_t)k * kPanel * kPanel + e];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) part[e] = t;
+}
+
 // Tb (kOB x kOB, column-major) = [[T1, -T1 G12 T2], [0, T2]] with G12 the sum of the partials
 // (fixed order); T1, T2 are the panels' 32 x 32 T, nb2 the second panel's width.
 __global__ void __launch_bounds__(256) k_tmerge(const double* T1, const double* T2, const double* part, int nparts,
@@ -747,12 +758,16 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
             kt_end(tk, 0.0, st);
             // merged T of the outer block
             const int64_t L2 = s - J0 - kPanel;
-            int gp = (int)std::min<int64_t>(e.gparts, std::max<int64_t>(1, ceil_div(L2, 512)));
+            int gp = (int)std::min<int64_t>(e.gparts, std::max<int64_t>(1, ceil_div(L2, 128)));
             const int64_t chunk = round_up(ceil_div(L2, gp), 64);
             gp = (int)ceil_div(L2, chunk);
             k_gram12<<<gp, 256, 0, st>>>(A, lda, s, J0, nb2, chunk, e.gpart);
             CSLS_CUDA(cudaGetLastError());
-            k_tmerge<<<1, 256, 0, st>>>(e.T1, q.T, e.gpart, gp, nb2, e.Tb);
+            // the partials of each Gram entry summed by a warp (in place into partial 0), so the
+            // single-CTA merge reads one value per entry
+            k_gsum<<<kPanel * kPanel / 8, 256, 0, st>>>(e.gpart, gp);
+            CSLS_CUDA(cudaGetLastError());
+            k_tmerge<<<1, 256, 0, st>>>(e.T1, q.T, e.gpart, 1, nb2, e.Tb);
             CSLS_CUDA(cudaGetLastError());
             nl += 6;
         } else {
