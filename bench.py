@@ -454,6 +454,9 @@ def main():
         h_c = torch.tensor(p.c).pin_memory()
         r_half = 0.5 / np.asarray(p.grid, dtype=np.float64)
         h2d = h_rows.numel() + h_k.numel() * 8 + h_c.numel() * 8 + h_b.numel() * 8
+        # one untimed assembly, so that its kernels are loaded like those of the factor and solve,
+        # which the timed steps above have already run
+        csls.csls_rfm_assemble(p.dim, r_half, p.J, h_k.cuda(), h_c.cuda(), h_rows.cuda())
     d2h = h_x.numel() * 8
     torch.cuda.synchronize()
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -258,9 +258,15 @@ typedef struct {
  * c (device, boxes x J). rows (device, nrows descriptors) fix the row order. Output (device,
  * caller-owned): row_ptr (nrows + 1), col and val (sum of the widths: J per row of kinds
  * 0-1, 2 J for 2-3; columns box-major, ascending within each row). Scratch: the
- * csls_rfm_assemble_workspace bytes. Errors: CSLS_ERR_ARG (dim not 2 or 3, J <= 0,
+ * csls_rfm_assemble_workspace bytes. Errors: CSLS_ERR_ARG (dim not 2 or 3, J outside 1..65536,
  * non-positive half-widths, NULL pointers). */
 int csls_rfm_assemble_workspace(int64_t nrows, size_t* bytes);
+/* The number of nonzeros csls_rfm_assemble will write for these rows (host output *nnz), so
+ * that the caller can size col and val: the widths summed on the device (rows and work as for
+ * csls_rfm_assemble); synchronises `stream` before it returns. Errors: CSLS_ERR_ARG (J outside
+ * 1..65536, nrows <= 0, NULL pointers), CSLS_ERR_WORKSPACE. */
+int csls_rfm_nnz(int64_t nrows, const csls_rfm_row* rows, int64_t J, void* work, size_t work_bytes,
+                 int64_t* nnz, csls_stream_t stream);
 int csls_rfm_assemble(int dim, const double* r_half, int64_t J, const double* k, const double* c,
                       int64_t nrows, const csls_rfm_row* rows, int64_t* row_ptr, int32_t* col,
                       double* val, void* work, size_t work_bytes, csls_stream_t stream);

@@ -77,6 +77,8 @@ EXPORTS = {
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "csls_factor_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "csls_rfm_assemble_workspace": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p]),
+    "csls_rfm_nnz": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]),
     "csls_rfm_assemble": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
@@ -329,14 +331,16 @@ def csls_rfm_assemble(dim, r_half, J, k, c, rows, stream=None):
     nrows = rows.numel() // 40
     assert rows.numel() == 40 * nrows and rows.dtype == torch.uint8
     dev = k.device
-    kind = rows.view(-1, 40)[:, 0:4].contiguous().view(torch.int32).view(-1)
-    nnz = int(torch.where(kind >= 2, 2 * J, J).sum().item())
-    row_ptr = torch.empty(nrows + 1, dtype=torch.int64, device=dev)
-    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
-    val = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
     nbytes = ctypes.c_size_t()
     _check(_lib().csls_rfm_assemble_workspace(nrows, ctypes.byref(nbytes)), "csls_rfm_assemble_workspace")
     work = _workspace(nbytes.value, dev)
+    nnz_h = ctypes.c_int64()
+    _check(_lib().csls_rfm_nnz(nrows, _ptr(rows), int(J), _ptr(work), work.numel(), ctypes.byref(nnz_h),
+                               _stream(stream)), "csls_rfm_nnz")
+    nnz = nnz_h.value
+    row_ptr = torch.empty(nrows + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    val = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
     rh = (ctypes.c_double * dim)(*[float(v) for v in r_half])
     _check(_lib().csls_rfm_assemble(int(dim), rh, int(J), _ptr(k.contiguous()), _ptr(c.contiguous()), nrows,
                                     _ptr(rows), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(work), work.numel(),

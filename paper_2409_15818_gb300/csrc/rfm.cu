@@ -22,6 +22,17 @@ __global__ void k_rfm_widths(const csls_rfm_row* rows, int64_t nrows, int J, int
         widths[i] = rows[i].kind >= 2 ? 2 * J : J;
 }
 
+// Sum of the row widths (the nnz of the assembled matrix); integer atomics, so the total does not
+// depend on the order in which the warps add.
+__global__ void k_rfm_count(const csls_rfm_row* rows, int64_t nrows, int J, unsigned long long* total) {
+    unsigned long long acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x)
+        acc += rows[i].kind >= 2 ? 2 * J : J;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
 template <int DIM>
 __device__ __forceinline__ double feature_z(const double* k, const double* c, int64_t f, const double* t) {
     double z = 0.0;
@@ -82,6 +93,26 @@ using namespace csls;
 int csls_rfm_assemble_workspace(int64_t nrows, size_t* bytes) {
     if (nrows <= 0 || !bytes) return CSLS_ERR_ARG;
     *bytes = (size_t)round_up(nrows * 4, 256);
+    return CSLS_OK;
+}
+
+int csls_rfm_nnz(int64_t nrows, const csls_rfm_row* rows, int64_t J, void* work, size_t work_bytes,
+                 int64_t* nnz, csls_stream_t stream) {
+    if (nrows <= 0 || !rows || J <= 0 || J > 65536 || !nnz) return CSLS_ERR_ARG;
+    size_t need = 0;
+    CSLS_TRY(csls_rfm_assemble_workspace(nrows, &need));
+    if (!work || work_bytes < need || ((uintptr_t)work & 255) != 0) return CSLS_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long* total = (unsigned long long*)work;
+    CSLS_CUDA(cudaMemsetAsync(total, 0, sizeof(*total), st));
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    const int g = (int)std::min<int64_t>(std::max<int64_t>(1, ceil_div(nrows, 256)), cap);
+    k_rfm_count<<<g, 256, 0, st>>>(rows, nrows, (int)J, total);
+    CSLS_CUDA(cudaGetLastError());
+    unsigned long long h = 0;
+    CSLS_CUDA(cudaMemcpyAsync(&h, total, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CSLS_CUDA(cudaStreamSynchronize(st));
+    *nnz = (int64_t)h;
     return CSLS_OK;
 }
 
