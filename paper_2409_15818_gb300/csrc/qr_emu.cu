@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "csls_internal.cuh"
+#include "tc.cuh"
 
 namespace csls {
 
@@ -166,6 +167,19 @@ __global__ void k_panel_top_to_f64(double* A, int64_t lda, int64_t j0, int nbw, 
 
 constexpr int kOB = 2 * kPanel;   // 64
 
+// Tiles of the tcgen05 update C += V Wn: 128 rows (one TMEM lane each) x 32 columns. Its digit
+// planes are stored tile by tile in the canonical K-major core-matrix order, so that one bulk
+// copy moves a plane into shared memory ready for the MMA: in a V plane tile the 16-byte chunk
+// holding row r, columns 8 kg .. 8 kg + 7 sits at chunk index kg x 128 + r (Wn planes: kg x 32 + c).
+constexpr int kTcM = 128;
+constexpr int kTcN = 32;
+__device__ __forceinline__ int64_t vd_chunk(int p, int64_t ntv, int64_t lr, int kg) {
+    return (((int64_t)p * ntv + (lr >> 7)) * 8 + kg) * kTcM + (lr & (kTcM - 1));
+}
+__device__ __forceinline__ int64_t wd_chunk(int q, int64_t ntw, int64_t c, int kg) {
+    return (((int64_t)q * ntw + (c >> 5)) * 8 + kg) * kTcN + (c & (kTcN - 1));
+}
+
 // Masked Householder vector entry of the outer block starting at J0: 0 above the diagonal,
 // 1 on it, the stored tail below.
 __device__ __forceinline__ double vmask(const double* A, int64_t lda, int64_t r, int64_t J0, int a) {
@@ -192,9 +206,9 @@ __global__ void __launch_bounds__(256) k_vcolmax(const double* A, int64_t lda, i
     if (threadIdx.x < nbo) atomicMax(&colmax[threadIdx.x], red[threadIdx.x]);
 }
 
-// Digits of V: per-row scale for C += V Wn (Vd[p][r][a], a contiguous) and per-column
-// scale for V^T C (VTd[p][a][r], r contiguous). Rows are local row indices r - J0; columns
-// a >= nbo and rows past the block are zero digits.
+// Digits of V: per-row scale for C += V Wn (Vd: plane tiles of 128 rows in core-matrix order,
+// ldv a multiple of 128) and per-column scale for V^T C (VTd[p][a][r], r contiguous). Rows are
+// local row indices r - J0; columns a >= nbo and rows past the block are zero digits.
 __global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, int64_t s, int64_t J0, int nbo,
                                                  const unsigned long long* colmax, int64_t ldv,
                                                  unsigned short* Vd, unsigned short* VTd, int* frow, int* ecol) {
@@ -213,9 +227,9 @@ __global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, i
             if (lr < L) mx = fmax(mx, fabs(vmask(A, lda, r, J0, a)));
         const int f = exp_of(mx);
         frow[lr] = f;
-        // the row-scaled digits of 8 consecutive columns go out as one 16-byte store per plane (a
-        // thread owns a row, so its 64 entries of a plane are contiguous); the column-scaled planes are
-        // written entry by entry, consecutive across the threads
+        // the row-scaled digits of 8 consecutive columns go out as one 16-byte chunk per plane
+        // (consecutive rows are consecutive chunks); the column-scaled planes are written entry by
+        // entry, consecutive across the threads
         for (int a0 = 0; a0 < kOB; a0 += 8) {
             uint32_t pk[kDig][4];
 #pragma unroll
@@ -235,7 +249,7 @@ __global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, i
             }
 #pragma unroll
             for (int p = 0; p < kDig; ++p)
-                *reinterpret_cast<uint4*>(Vd + ((int64_t)p * ldv + lr) * kOB + a0) =
+                reinterpret_cast<uint4*>(Vd)[vd_chunk(p, ldv / kTcM, lr, a0 >> 3)] =
                     make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
         }
     }
@@ -274,7 +288,8 @@ __global__ void __launch_bounds__(256) k_wreduce_ob(const double* Wp, int ks, co
     }
 }
 
-// Digits of Wn (kOB x nprime, row-major): per-column scale; Wd[p][c][a].
+// Digits of Wn (kOB x nprime, row-major): per-column scale; Wd in plane tiles of 32 columns in
+// core-matrix order (ldw a multiple of 32).
 __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw, unsigned short* Wd, int* gcol) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ldw; c += (int64_t)gridDim.x * blockDim.x) {
         double mx = 0.0;
@@ -282,7 +297,7 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
             if (c < nprime) mx = fmax(mx, fabs(Wn[(int64_t)a * nprime + c]));
         const int g = exp_of(mx);
         gcol[c] = g;
-        for (int a0 = 0; a0 < kOB; a0 += 8) {   // 16-byte stores, as in k_vdigits
+        for (int a0 = 0; a0 < kOB; a0 += 8) {   // 16-byte chunks, as in k_vdigits
             uint32_t pk[kDig][4];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -299,7 +314,7 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
             }
 #pragma unroll
             for (int p = 0; p < kDig; ++p)
-                *reinterpret_cast<uint4*>(Wd + ((int64_t)p * ldw + c) * kOB + a0) =
+                reinterpret_cast<uint4*>(Wd)[wd_chunk(p, ldw / kTcN, c, a0 >> 3)] =
                     make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
         }
     }
@@ -515,139 +530,212 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, 
         }
 }
 
-// ------------------------------------------------------------------ C += V Wn  (exact integer update)
+// ------------------------------------------------------------------ C += V Wn  (exact integer update, tcgen05)
 
-constexpr int kUpdRows = 64, kUpdPad = 8, kUpdLdk = kOB + kUpdPad;   // 72
+// One CTA per SM owns a 128-row tile of C and walks `cpt` consecutive 32-column tiles. Roles:
+//   warp 0 (one thread)  bulk copies: the V digit planes of the row tile once, then per column
+//                        tile the Wn digit planes and the 32 C columns (rows contiguous) into one
+//                        of two stages;
+//   warp 1 (one thread)  tcgen05.mma: per level l the products of digit pairs p + q = l
+//                        accumulate in their own FP32 TMEM block (exact: every level sum is an
+//                        integer below 6 x 64 x 2^14 < 2^23); two accumulator sets of 6 x 32
+//                        columns, so the MMAs of tile i + 1 run while tile i is written back;
+//   warps 2..9           epilogue: TMEM -> registers, levels combined in int64, scaled onto the
+//                        column's fixed-point grid and added to the staged C entry; one thread
+//                        per row and 16 columns, so each column store of a warp is 256
+//                        contiguous bytes.
+// Every wait is bounded (spin polls and 2 s of wall time); a role that gives up sets the CTA's
+// abort flag and the error word, and the CTA still waits for its copies and MMAs in flight and
+// frees its tensor memory before it returns.
+constexpr int kTcLevels = kLev + 1;
+constexpr int kTcPlaneA = kTcM * kOB * 2;        // bytes of one V digit plane tile (16 KB)
+constexpr int kTcPlaneB = kTcN * kOB * 2;        // bytes of one Wn digit plane tile (4 KB)
+constexpr int kTcBufCols = kTcLevels * kTcN;     // TMEM columns of one accumulator set (192)
+constexpr int kTcTmemCols = 512;
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
+constexpr unsigned long long kTcWaitNs = 2000000000ULL;
 
-template <int UC>
-struct UpdSmem {
-    unsigned short Vs[kDig][kUpdRows][kUpdLdk];   // [p][r][a]
-    unsigned short Ws[kDig][UC][kUpdLdk];         // [q][c][a]
-    int frow[kUpdRows];
-    int gcol[UC];
-    int ecol[UC];
+struct TcUpdSmem {
+    unsigned char A[kDig][kTcPlaneA];
+    unsigned char B[2][kDig][kTcPlaneB];
+    long long C[2][kTcN][kTcM];
+    uint64_t full_a, full[2], done[2], freed[2], drain;
+    uint32_t tmem;
+    int abort;
 };
 
-// C tile of 64 rows x UC columns; 8 warps as 2 (rows) x 4 (columns), each warp 32 rows x UC/4 columns
-// (NT n8 tiles). KM: products over the first KM digit columns (64, or 32 when the outer block has
-// one panel). MB: CTAs per SM the register budget is sized for.
-template <int KM, int UC, int MB>
-__global__ void __launch_bounds__(kEmuThreads, MB)
-k_emu_update(long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int nbo, const unsigned short* Vd,
-             int64_t ldv, const int* frow, const unsigned short* Wd, int64_t ldw, const int* gcol, const int* E,
-             int64_t nprime) {
-    constexpr int NT = UC / 32;   // n8 tiles per warp
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    UpdSmem<UC>& sm = *reinterpret_cast<UpdSmem<UC>*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int64_t jc = J0 + nbo;
-    const int64_t L = s - J0;
-    const int64_t rb = (int64_t)blockIdx.x * kUpdRows;   // local row of tile row 0
-    const int64_t cb = (int64_t)blockIdx.y * UC;         // trailing column of tile col 0
-    const int wm = warp & 1, wn = warp >> 1;             // warp tile: rows wm*32..+32, cols wn*(UC/4)..
-    // digit tiles: each row of 64 bf16 is 8 chunks of 16 B
-    for (int idx = tid; idx < kDig * kUpdRows * 8; idx += kEmuThreads) {
-        const int ch = idx & 7, r = (idx >> 3) % kUpdRows, p = (idx >> 3) / kUpdRows;
-        const int64_t lr = rb + r;
-        const bool ok = lr < L;
-        cp_async16(&sm.Vs[p][r][ch * 8], Vd + ((int64_t)p * ldv + (ok ? lr : 0)) * kOB + ch * 8, ok ? 16 : 0);
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, const unsigned short* Vd, int64_t ntv,
+                const int* frow, const unsigned short* Wd, int64_t ntw, const int* gcol, const int* E, int64_t nprime,
+                int cpt, long long spin, int* err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    TcUpdSmem& sm = *reinterpret_cast<TcUpdSmem*>(tc_smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t L = s - J0, jc = J0 + nbo;
+    const int64_t rt = blockIdx.y, rb = rt * kTcM;
+    const int64_t nct = (nprime + kTcN - 1) / kTcN;
+    const int64_t ct0 = (int64_t)blockIdx.x * cpt;
+    const int ntile = (int)(nct - ct0 < cpt ? nct - ct0 : cpt);
+    volatile int* abort = &sm.abort;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&sm.full_a, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&sm.full[b], 1);
+            tc::mbar_init(&sm.done[b], 1);
+            tc::mbar_init(&sm.freed[b], 32 * kTcEpiWarps);
+        }
+        tc::mbar_init(&sm.drain, 1);
+        sm.abort = 0;
+        tc::mbar_init_fence();
     }
-    for (int idx = tid; idx < kDig * UC * 8; idx += kEmuThreads) {
-        const int ch = idx & 7, c = (idx >> 3) % UC, q = (idx >> 3) / UC;
-        const int64_t col = cb + c;
-        const bool ok = col < nprime;
-        cp_async16(&sm.Ws[q][c][ch * 8], Wd + ((int64_t)q * ldw + (ok ? col : 0)) * kOB + ch * 8, ok ? 16 : 0);
-    }
-    cp_async_commit();
-    // this warp's C entries are loaded while the digit tiles are in flight; they are only
-    // needed after the products
-    long long cval[2][NT][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int64_t lr = rb + wm * 32 + i * 16 + g + (h >> 1) * 8;
-                const int64_t col = cb + wn * (UC / 4) + j * 8 + 2 * t + (h & 1);
-                cval[i][j][h] = (lr < L && col < nprime) ? Cfix[(J0 + lr) + (jc + col) * lda] : 0LL;
-            }
-    for (int i = tid; i < kUpdRows; i += kEmuThreads) sm.frow[i] = rb + i < L ? frow[rb + i] : 0;
-    for (int i = tid; i < UC; i += kEmuThreads) {
-        sm.gcol[i] = cb + i < nprime ? gcol[cb + i] : 0;
-        sm.ecol[i] = cb + i < nprime ? E[jc + cb + i] : 0;
-    }
-    cp_async_wait<0>();
+    if (warp == 1) tc::tmem_alloc(&sm.tmem, kTcTmemCols);
+    tc::fence_before_sync();
     __syncthreads();
-    long long acc64[2][NT][4];
-#pragma unroll 1
-    for (int l = 0; l <= kLev; ++l) {
-        float acc[2][NT][4];
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < NT; ++j)
-#pragma unroll
-                for (int h = 0; h < 4; ++h) acc[i][j][h] = 0.0f;
-        for (int p = 0; p <= l; ++p) {
-            const int q = l - p;
-#pragma unroll
-            for (int ks = 0; ks < KM; ks += 16) {
-                uint32_t af[2][4], bq[NT / 2][4];
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-                    ldsm_x4(af[i], &sm.Vs[p][wm * 32 + i * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
-#pragma unroll
-                for (int jj = 0; jj < NT / 2; ++jj)
-                    ldsm_x4(bq[jj], &sm.Ws[q][wn * (UC / 4) + jj * 16 + (lane & 7) + ((lane >> 4) & 1) * 8]
-                                         [ks + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int jj = 0; jj < NT / 2; ++jj) {
-                        const uint32_t b0[2] = {bq[jj][0], bq[jj][1]}, b1[2] = {bq[jj][2], bq[jj][3]};
-                        hmma(acc[i][2 * jj], af[i], b0);
-                        hmma(acc[i][2 * jj + 1], af[i], b1);
+    tc::fence_after_sync();
+    const uint32_t tmem = sm.tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const int64_t rows = L - rb < kTcM ? L - rb : kTcM;
+            const uint32_t cbytes = (uint32_t)(((rows + 1) & ~1LL) * 8);   // whole 16-byte units, within lda
+            int armed0 = 0, armed1 = 0;   // uses of each stage whose copies were issued
+            tc::mbar_arrive_expect_tx(&sm.full_a, kDig * kTcPlaneA);
+            for (int p = 0; p < kDig; ++p)
+                tc::bulk_g2s(sm.A[p], reinterpret_cast<const unsigned char*>(Vd) + ((int64_t)p * ntv + rt) * kTcPlaneA,
+                             kTcPlaneA, &sm.full_a);
+            for (int i = 0; i < ntile; ++i) {
+                const int b = i & 1, u = i >> 1;
+                if (u > 0 && !tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
+                    *abort = 1;
+                    set_error(err, CSLS_ERR_TIMEOUT);
+                    break;
+                }
+                const int64_t ct = ct0 + i;
+                const int ncols = (int)(nprime - ct * kTcN < kTcN ? nprime - ct * kTcN : kTcN);
+                tc::mbar_arrive_expect_tx(&sm.full[b], kDig * kTcPlaneB + ncols * cbytes);
+                if (b) armed1 = u + 1;
+                else armed0 = u + 1;
+                for (int q = 0; q < kDig; ++q)
+                    tc::bulk_g2s(sm.B[b][q],
+                                 reinterpret_cast<const unsigned char*>(Wd) + ((int64_t)q * ntw + ct) * kTcPlaneB,
+                                 kTcPlaneB, &sm.full[b]);
+                for (int c = 0; c < ncols; ++c)
+                    tc::bulk_g2s(sm.C[b][c], Cfix + (J0 + rb) + (jc + ct * kTcN + c) * lda, cbytes, &sm.full[b]);
+            }
+            // copies in flight land before the CTA can leave
+            tc::mbar_wait(&sm.full_a, 0, spin, kTcWaitNs, nullptr);
+            if (armed0) tc::mbar_wait(&sm.full[0], (armed0 - 1) & 1, spin, kTcWaitNs, nullptr);
+            if (armed1) tc::mbar_wait(&sm.full[1], (armed1 - 1) & 1, spin, kTcWaitNs, nullptr);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool issued = false;
+            if (tc::mbar_wait(&sm.full_a, 0, spin, kTcWaitNs, abort)) {
+                const uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
+                const uint32_t a0 = tc::smem_addr(sm.A[0]);
+                const int ksteps = (nbo + 15) >> 4;   // digit columns past nbo are zero
+                for (int i = 0; i < ntile; ++i) {
+                    const int b = i & 1, u = i >> 1;
+                    if (!tc::mbar_wait(&sm.full[b], u & 1, spin, kTcWaitNs, abort)) {
+                        *abort = 1;
+                        set_error(err, CSLS_ERR_TIMEOUT);
+                        break;
                     }
+                    tc::fence_after_sync();
+                    const uint32_t b0 = tc::smem_addr(sm.B[b][0]);
+                    const uint32_t d0 = tmem + (uint32_t)(b * kTcBufCols);
+                    for (int l = 0; l <= kLev; ++l)
+                        for (int p = 0; p <= l; ++p)
+                            for (int k = 0; k < ksteps; ++k) {
+                                // K step of 16 = two core-matrix columns
+                                const uint64_t ad = tc::smem_desc(a0 + p * kTcPlaneA + k * 2 * (kTcM * 16), kTcM * 16, 128);
+                                const uint64_t bd =
+                                    tc::smem_desc(b0 + (l - p) * kTcPlaneB + k * 2 * (kTcN * 16), kTcN * 16, 128);
+                                tc::mma_bf16(d0 + l * kTcN, ad, bd, idesc, (p | k) != 0);
+                            }
+                    tc::mma_commit(&sm.done[b]);
+                    issued = true;
+                }
+            } else {
+                *abort = 1;
+                set_error(err, CSLS_ERR_TIMEOUT);
+            }
+            if (issued) {   // every MMA has completed before the tensor memory is freed
+                tc::mma_commit(&sm.drain);
+                tc::mbar_wait(&sm.drain, 0, spin, kTcWaitNs, nullptr);
             }
         }
-        // every level sum is an integer below 6 x 64 x 2^14 < 2^24: exact in FP32
+        __syncwarp();
+    } else {
+        const int quarter = warp & 3;              // a warp reads TMEM lanes 32 (warp % 4) .. + 31
+        const int half = (warp - 2) >> 2;          // columns 16 half .. + 15 of each tile
+        const int r = quarter * 32 + lane;
+        const int64_t lr = rb + r;
+        const bool rok = lr < L;
+        const int fr = rok ? frow[lr] : 0;
+        for (int i = 0; i < ntile; ++i) {
+            const int b = i & 1, u = i >> 1;
+            bool ok = tc::mbar_wait(&sm.done[b], u & 1, spin, kTcWaitNs, abort) &&
+                      tc::mbar_wait(&sm.full[b], u & 1, spin, kTcWaitNs, abort);
+            ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld is warp-wide
+            if (!ok) {
+                *abort = 1;
+                set_error(err, CSLS_ERR_TIMEOUT);
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTcBufCols + half * 16);
+            uint32_t v[kTcLevels][16];
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+            for (int l = 0; l < kTcLevels; ++l) tc::tmem_ld16(ta + l * kTcN, v[l]);
+            tc::tmem_ld_wait();
+            tc::fence_before_sync();
+            const int64_t cbase = (ct0 + i) * kTcN + half * 16;
 #pragma unroll
-            for (int j = 0; j < NT; ++j)
+            for (int j = 0; j < 16; ++j) {
+                const int64_t col = cbase + j;
+                if (rok && col < nprime) {
+                    long long acc = 0;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const long long v = (long long)__float2int_rn(acc[i][j][h]);
-                    acc64[i][j][h] = l == 0 ? v : (acc64[i][j][h] << 8) + v;
-                }
-    }
-    // Cfix += acc64 * 2^(f_r + g_c - 14 - 8 kLev + 62 - E_c), rounded to the fixed-point grid
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int r = wm * 32 + i * 16 + g + (h >> 1) * 8;
-                const int c = wn * (UC / 4) + j * 8 + 2 * t + (h & 1);
-                const int64_t lr = rb + r, col = cb + c;
-                if (lr < L && col < nprime) {
-                    const int sh = sm.frow[r] + sm.gcol[c] - 14 - 8 * kLev + kFixBits - sm.ecol[c];
-                    const long long v = acc64[i][j][h];
+                    for (int l = 0; l < kTcLevels; ++l)
+                        acc = acc * 256 + (long long)__float2int_rn(__uint_as_float(v[l][j]));
+                    // Cfix += acc * 2^(f_r + g_c - 14 - 8 kLev + 62 - E_c), rounded to the fixed-point grid
+                    const int sh = fr + gcol[col] - 14 - 8 * kLev + kFixBits - E[jc + col];
                     long long dlt;
-                    if (v == 0) dlt = 0;
-                    else if (sh >= 0) dlt = sh < 63 ? v << sh : 0;
-                    else dlt = -sh < 63 ? (v + (1LL << (-sh - 1))) >> (-sh) : 0;
-                    Cfix[(J0 + lr) + (jc + col) * lda] = cval[i][j][h] + dlt;
+                    if (acc == 0) dlt = 0;
+                    else if (sh >= 0) dlt = sh < 63 ? acc << sh : 0;
+                    else dlt = -sh < 63 ? (acc + (1LL << (-sh - 1))) >> (-sh) : 0;
+                    Cfix[(J0 + lr) + (jc + col) * lda] = sm.C[b][half * 16 + j][r] + dlt;
                 }
             }
+            tc::mbar_arrive(&sm.freed[b]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kTcTmemCols);
+    }
 }
 
-// Tile width of the update: 64 columns, 2 CTAs per SM (measured faster than 128 columns with one CTA
-// per SM and 32 x 32 warp tiles: 0.75 s against 0.70 s per factor on the 2D bench workload).
-constexpr int kUpdCols = 64;
-constexpr int kUpdMinBlocks = kUpdCols == 64 ? 2 : 1;
+// Column tiles per CTA: the split of each row tile's columns that minimises the waves of
+// one-CTA-per-SM launches times the tiles a CTA walks (plus ~2 tiles for its V planes and the
+// pipeline fill).
+static int tc_update_cpt(int64_t nrt, int64_t nct, int sms) {
+    int best = (int)nct;
+    double best_cost = 1e300;
+    for (int64_t c = 1; c <= nct; ++c) {
+        const int64_t ncs = (nct + c - 1) / c;
+        const double cost = (double)((nrt * ncs + sms - 1) / sms) * (double)(c + 2);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = (int)c;
+        }
+    }
+    return best;
+}
 
 // ------------------------------------------------------------------ scratch and driver
 
@@ -657,9 +745,9 @@ struct EmuScratch {
     int* ecol;                    // kOB
     int* frow;                    // s
     int* gcol;                    // n
-    unsigned short* Vd;           // kDig * s * kOB
+    unsigned short* Vd;           // kDig * s * kOB (s rounded up to 128)
     unsigned short* VTd;          // kDig * kOB * s
-    unsigned short* Wd;           // kDig * n * kOB
+    unsigned short* Wd;           // kDig * n * kOB (n rounded up to 32)
     double* Wp;                   // split-K partials of W (kOB x n per chunk)
     int64_t wp_elems;
     double* Wn;                   // kOB x n
@@ -676,7 +764,7 @@ static int64_t emu_wp_elems(int64_t n) {
 }
 
 static EmuScratch emu_carve(Carve& c, int64_t s, int64_t n) {
-    const int64_t ldv = round_up(s, 8), ldw = round_up(n, 8);
+    const int64_t ldv = round_up(s, kTcM), ldw = round_up(n, kTcN);
     EmuScratch e;
     e.E = c.take<int>((size_t)n);
     e.colmax = c.take<unsigned long long>(kOB);
@@ -711,18 +799,16 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     if (emu_bytes < qr_emu_scratch_bytes(s, n)) return CSLS_ERR_WORKSPACE;
     Carve c{(char*)emu_work, 0, emu_bytes, false};
     EmuScratch e = emu_carve(c, s, n);
-    const int64_t ldv = round_up(s, 8);
+    // the update's bulk copies read C columns from 16-byte boundaries
+    if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda & 1) != 0) return CSLS_ERR_ARG;
     static bool attr = false;
     if (!attr) {
         CSLS_CUDA(cudaFuncSetAttribute(k_emu_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(VtcSmem)));
-        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kOB, kUpdCols, kUpdMinBlocks>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpdSmem<kUpdCols>)));
-        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update<kPanel, kUpdCols, kUpdMinBlocks>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpdSmem<kUpdCols>)));
+        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(TcUpdSmem)));
         CSLS_CUDA(cudaFuncSetAttribute(k_wreduce_ob, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWrSmem));
         attr = true;
     }
-    (void)ldv;
     const int sms = device_sm_count();
     CSLS_CUDA(cudaMemsetAsync(q.bar, 0, sizeof(GridBarrier), st));
     k_col_exponent<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, st>>>(A, lda, s, n, e.E);
@@ -782,7 +868,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         k_vcolmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 4), (int64_t)sms * 4)), 256, 0, st>>>(
             A, lda, s, J0, nbo, e.colmax);
         CSLS_CUDA(cudaGetLastError());
-        const int64_t ldvp = round_up(L, 8);   // digit planes use the current block height
+        const int64_t ldvp = round_up(L, kTcM);   // digit planes use the current block height
         k_vdigits<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ldvp, 256), (int64_t)sms * 8)), 256, 0, st>>>(
             A, lda, s, J0, nbo, e.colmax, ldvp, e.Vd, e.VTd, e.frow, e.ecol);
         CSLS_CUDA(cudaGetLastError());
@@ -805,21 +891,16 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         k_wreduce_ob<<<(unsigned)ceil_div(nprime, kWrCols), 256, kWrSmem, st>>>(e.Wp, (int)ks, e.Tb, nbo, e.Wn, nprime);
         CSLS_CUDA(cudaGetLastError());
         // digits of Wn, then the exact update
-        const int64_t ldwp = round_up(nprime, 8);
+        const int64_t ldwp = round_up(nprime, kTcN);
         k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 256)), 256, 0, st>>>(e.Wn, nbo, nprime, ldwp, e.Wd,
                                                                                         e.gcol);
         CSLS_CUDA(cudaGetLastError());
         tk = kt_begin(kFamUpdate, st);
-        const dim3 ug((unsigned)ceil_div(L, kUpdRows), (unsigned)ceil_div(nprime, kUpdCols));
-        const size_t usm = sizeof(UpdSmem<kUpdCols>);
-        if (nbo > kPanel)   // zero digits past nbo need no products
-            k_emu_update<kOB, kUpdCols, kUpdMinBlocks><<<ug, kEmuThreads, usm, st>>>(
-                reinterpret_cast<long long*>(A), lda, s, n, J0, nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp, e.gcol, e.E,
-                nprime);
-        else
-            k_emu_update<kPanel, kUpdCols, kUpdMinBlocks><<<ug, kEmuThreads, usm, st>>>(
-                reinterpret_cast<long long*>(A), lda, s, n, J0, nbo, e.Vd, ldvp, e.frow, e.Wd, ldwp, e.gcol, e.E,
-                nprime);
+        const int64_t nrt = ceil_div(L, kTcM), nct = ceil_div(nprime, kTcN);
+        const int cpt = tc_update_cpt(nrt, nct, sms);
+        k_emu_update_tc<<<dim3((unsigned)ceil_div(nct, cpt), (unsigned)nrt), kTcThreads, sizeof(TcUpdSmem), st>>>(
+            reinterpret_cast<long long*>(A), lda, s, J0, nbo, e.Vd, ldvp / kTcM, e.frow, e.Wd, ldwp / kTcN, e.gcol, e.E,
+            nprime, cpt, spin, err);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
         nl += 7;
