@@ -491,7 +491,7 @@ def main():
     # time summed over its launches (algorithmic flops per launch / average launch time)
     qr_gflops = qr_flops(s, n) / (statistics.median(qr_ms) * 1e-3) / 1e9
     fam_names = {"f64emu": ["k_panel (FP64 Householder panel)", "k_emu_vtc (W = V^T C, exact bf16 digit products)",
-                            "k_emu_update (C -= V W, exact bf16 digit products)"],
+                            "k_emu_update_tc (C -= V W, exact bf16 digit products on tcgen05)"],
                  "f64": ["k_panel (FP64 Householder panel)", "k_vtc_f64 (W = V^T C, DMMA)",
                          "k_update_f64 (C -= V W, DMMA)"],
                  "f32": ["k_panel (FP32 Householder panel)", "k_vtc_f32 (W = V^T C, FP32 FMA)",
@@ -507,13 +507,7 @@ def main():
         pairs = 21
         ach = pairs * kern_flop[top] / top_s / 1e12
         peak = bf16_sus
-        traffic = None
-        if top == 2:
-            # DRAM bytes per average launch: the ncu capture of one k_emu_update launch (2D RFM 6x6
-            # boxes, L=25,600 x n'=3,936, 64-column outer block) read+wrote 1.624 GB for 1.612 GB of C
-            # traffic (int64, read and written); traffic scales with L n', so the average launch here
-            # moves 1.007 x its algorithmic 16 L n' bytes (sum of L n' = flops / 128)
-            traffic = 1.007 * (kern_flop[2] / 8.0) / max(kern_n[2], 1)
+        traffic = None   # no ncu capture of the current dominant kernels yet
         roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on a smaller "

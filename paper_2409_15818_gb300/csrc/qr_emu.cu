@@ -23,6 +23,9 @@
 // when it becomes part of a panel; the panel is factored in FP64 by k_panel.
 #include <algorithm>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "csls_internal.cuh"
 #include "tc.cuh"
 
@@ -168,16 +171,17 @@ __global__ void k_panel_top_to_f64(double* A, int64_t lda, int64_t j0, int nbw, 
 constexpr int kOB = 2 * kPanel;   // 64
 
 // Tiles of the tcgen05 update C += V Wn: 128 rows (one TMEM lane each) x 32 columns. Its digit
-// planes are stored tile by tile in the canonical K-major core-matrix order, so that one bulk
-// copy moves a plane into shared memory ready for the MMA: in a V plane tile the 16-byte chunk
-// holding row r, columns 8 kg .. 8 kg + 7 sits at chunk index kg x 128 + r (Wn planes: kg x 32 + c).
+// planes are stored tile by tile (the 6 planes of a tile contiguous) in the canonical K-major
+// core-matrix order, so that one bulk copy moves a tile's planes into shared memory ready for
+// the MMA: in a V plane the 16-byte chunk holding row r, columns 8 kg .. 8 kg + 7 sits at chunk
+// index kg x 128 + r (Wn planes: kg x 32 + c).
 constexpr int kTcM = 128;
 constexpr int kTcN = 32;
-__device__ __forceinline__ int64_t vd_chunk(int p, int64_t ntv, int64_t lr, int kg) {
-    return (((int64_t)p * ntv + (lr >> 7)) * 8 + kg) * kTcM + (lr & (kTcM - 1));
+__device__ __forceinline__ int64_t vd_chunk(int p, int64_t lr, int kg) {
+    return (((lr >> 7) * kDig + p) * 8 + kg) * kTcM + (lr & (kTcM - 1));
 }
-__device__ __forceinline__ int64_t wd_chunk(int q, int64_t ntw, int64_t c, int kg) {
-    return (((int64_t)q * ntw + (c >> 5)) * 8 + kg) * kTcN + (c & (kTcN - 1));
+__device__ __forceinline__ int64_t wd_chunk(int q, int64_t c, int kg) {
+    return (((c >> 5) * kDig + q) * 8 + kg) * kTcN + (c & (kTcN - 1));
 }
 
 // Masked Householder vector entry of the outer block starting at J0: 0 above the diagonal,
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, i
             }
 #pragma unroll
             for (int p = 0; p < kDig; ++p)
-                reinterpret_cast<uint4*>(Vd)[vd_chunk(p, ldv / kTcM, lr, a0 >> 3)] =
+                reinterpret_cast<uint4*>(Vd)[vd_chunk(p, lr, a0 >> 3)] =
                     make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
         }
     }
@@ -314,7 +318,7 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
             }
 #pragma unroll
             for (int p = 0; p < kDig; ++p)
-                reinterpret_cast<uint4*>(Wd)[wd_chunk(p, ldw / kTcN, c, a0 >> 3)] =
+                reinterpret_cast<uint4*>(Wd)[wd_chunk(p, c, a0 >> 3)] =
                     make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
         }
     }
@@ -533,9 +537,11 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, 
 // ------------------------------------------------------------------ C += V Wn  (exact integer update, tcgen05)
 
 // One CTA per SM owns a 128-row tile of C and walks `cpt` consecutive 32-column tiles. Roles:
-//   warp 0 (one thread)  bulk copies: the V digit planes of the row tile once, then per column
-//                        tile the Wn digit planes and the 32 C columns (rows contiguous) into one
-//                        of two stages;
+//   warp 0 (one thread)  copies: the V digit planes of the row tile once (one bulk copy), then
+//                        per column tile its Wn digit planes (one bulk copy) and its 128 x 32 C
+//                        block (one 2D tensor copy; rows past s and columns past n read as zero)
+//                        into one of two stages, on separate barriers so the MMAs never wait
+//                        for C;
 //   warp 1 (one thread)  tcgen05.mma: per level l the products of digit pairs p + q = l
 //                        accumulate in their own FP32 TMEM block (exact: every level sum is an
 //                        integer below 6 x 64 x 2^14 < 2^23); two accumulator sets of 6 x 32
@@ -560,15 +566,24 @@ struct TcUpdSmem {
     unsigned char A[kDig][kTcPlaneA];
     unsigned char B[2][kDig][kTcPlaneB];
     long long C[2][kTcN][kTcM];
-    uint64_t full_a, full[2], done[2], freed[2], drain;
+    uint64_t full_a, full_b[2], full_c[2], done[2], freed[2], drain;
     uint32_t tmem;
     int abort;
 };
 
+// 2D tiled tensor copy global -> shared (box of the tensor map at coordinates x, y)
+__device__ __forceinline__ void tensor_g2s_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            tc::smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(tc::smem_addr(bar))
+        : "memory");
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, const unsigned short* Vd, int64_t ntv,
-                const int* frow, const unsigned short* Wd, int64_t ntw, const int* gcol, const int* E, int64_t nprime,
-                int cpt, long long spin, int* err) {
+k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo,
+                const unsigned short* Vd, const int* frow, const unsigned short* Wd, const int* gcol, const int* E,
+                int64_t nprime, int cpt, long long spin, int* err) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     TcUpdSmem& sm = *reinterpret_cast<TcUpdSmem*>(tc_smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -578,10 +593,16 @@ k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, co
     const int64_t ct0 = (int64_t)blockIdx.x * cpt;
     const int ntile = (int)(nct - ct0 < cpt ? nct - ct0 : cpt);
     volatile int* abort = &sm.abort;
+    // tensor copies write shared memory at 128-byte boundaries: the staging area must start on one
+    if ((tc::smem_addr(tc_smem_raw) & 127) != 0) {
+        if (threadIdx.x == 0) set_error(err, CSLS_ERR_ARG);
+        return;
+    }
     if (threadIdx.x == 0) {
         tc::mbar_init(&sm.full_a, 1);
         for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&sm.full[b], 1);
+            tc::mbar_init(&sm.full_b[b], 1);
+            tc::mbar_init(&sm.full_c[b], 1);
             tc::mbar_init(&sm.done[b], 1);
             tc::mbar_init(&sm.freed[b], 32 * kTcEpiWarps);
         }
@@ -597,13 +618,10 @@ k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, co
 
     if (warp == 0) {
         if (lane == 0) {
-            const int64_t rows = L - rb < kTcM ? L - rb : kTcM;
-            const uint32_t cbytes = (uint32_t)(((rows + 1) & ~1LL) * 8);   // whole 16-byte units, within lda
             int armed0 = 0, armed1 = 0;   // uses of each stage whose copies were issued
             tc::mbar_arrive_expect_tx(&sm.full_a, kDig * kTcPlaneA);
-            for (int p = 0; p < kDig; ++p)
-                tc::bulk_g2s(sm.A[p], reinterpret_cast<const unsigned char*>(Vd) + ((int64_t)p * ntv + rt) * kTcPlaneA,
-                             kTcPlaneA, &sm.full_a);
+            tc::bulk_g2s(sm.A[0], reinterpret_cast<const unsigned char*>(Vd) + rt * (kDig * kTcPlaneA),
+                         kDig * kTcPlaneA, &sm.full_a);
             for (int i = 0; i < ntile; ++i) {
                 const int b = i & 1, u = i >> 1;
                 if (u > 0 && !tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
@@ -612,21 +630,24 @@ k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, co
                     break;
                 }
                 const int64_t ct = ct0 + i;
-                const int ncols = (int)(nprime - ct * kTcN < kTcN ? nprime - ct * kTcN : kTcN);
-                tc::mbar_arrive_expect_tx(&sm.full[b], kDig * kTcPlaneB + ncols * cbytes);
+                tc::mbar_arrive_expect_tx(&sm.full_b[b], kDig * kTcPlaneB);
+                tc::bulk_g2s(sm.B[b][0], reinterpret_cast<const unsigned char*>(Wd) + ct * (kDig * kTcPlaneB),
+                             kDig * kTcPlaneB, &sm.full_b[b]);
+                tc::mbar_arrive_expect_tx(&sm.full_c[b], kTcN * kTcM * 8);
+                tensor_g2s_2d(sm.C[b][0], &cmap, (int)(J0 + rb), (int)(jc + ct * kTcN), &sm.full_c[b]);
                 if (b) armed1 = u + 1;
                 else armed0 = u + 1;
-                for (int q = 0; q < kDig; ++q)
-                    tc::bulk_g2s(sm.B[b][q],
-                                 reinterpret_cast<const unsigned char*>(Wd) + ((int64_t)q * ntw + ct) * kTcPlaneB,
-                                 kTcPlaneB, &sm.full[b]);
-                for (int c = 0; c < ncols; ++c)
-                    tc::bulk_g2s(sm.C[b][c], Cfix + (J0 + rb) + (jc + ct * kTcN + c) * lda, cbytes, &sm.full[b]);
             }
             // copies in flight land before the CTA can leave
             tc::mbar_wait(&sm.full_a, 0, spin, kTcWaitNs, nullptr);
-            if (armed0) tc::mbar_wait(&sm.full[0], (armed0 - 1) & 1, spin, kTcWaitNs, nullptr);
-            if (armed1) tc::mbar_wait(&sm.full[1], (armed1 - 1) & 1, spin, kTcWaitNs, nullptr);
+            if (armed0) {
+                tc::mbar_wait(&sm.full_b[0], (armed0 - 1) & 1, spin, kTcWaitNs, nullptr);
+                tc::mbar_wait(&sm.full_c[0], (armed0 - 1) & 1, spin, kTcWaitNs, nullptr);
+            }
+            if (armed1) {
+                tc::mbar_wait(&sm.full_b[1], (armed1 - 1) & 1, spin, kTcWaitNs, nullptr);
+                tc::mbar_wait(&sm.full_c[1], (armed1 - 1) & 1, spin, kTcWaitNs, nullptr);
+            }
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -638,7 +659,9 @@ k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, co
                 const int ksteps = (nbo + 15) >> 4;   // digit columns past nbo are zero
                 for (int i = 0; i < ntile; ++i) {
                     const int b = i & 1, u = i >> 1;
-                    if (!tc::mbar_wait(&sm.full[b], u & 1, spin, kTcWaitNs, abort)) {
+                    // the accumulator set of this stage was drained by the epilogue of tile i - 2
+                    if ((u > 0 && !tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) ||
+                        !tc::mbar_wait(&sm.full_b[b], u & 1, spin, kTcWaitNs, abort)) {
                         *abort = 1;
                         set_error(err, CSLS_ERR_TIMEOUT);
                         break;
@@ -678,7 +701,7 @@ k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, co
         for (int i = 0; i < ntile; ++i) {
             const int b = i & 1, u = i >> 1;
             bool ok = tc::mbar_wait(&sm.done[b], u & 1, spin, kTcWaitNs, abort) &&
-                      tc::mbar_wait(&sm.full[b], u & 1, spin, kTcWaitNs, abort);
+                      tc::mbar_wait(&sm.full_c[b], u & 1, spin, kTcWaitNs, abort);
             ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld is warp-wide
             if (!ok) {
                 *abort = 1;
@@ -718,6 +741,30 @@ k_emu_update_tc(long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo, co
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, kTcTmemCols);
     }
+}
+
+// Tensor map of the int64 trailing matrix for the update's C tiles: rows (contiguous, s of
+// them) x columns (n, stride lda), 128 x 32 boxes, zero fill outside.
+static int make_c_map(CUtensorMap* map, void* A, int64_t lda, int64_t s, int64_t n) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return CSLS_ERR_CUDA;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)s, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)lda * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcM, (cuuint32_t)kTcN};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, A, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return CSLS_ERR_CUDA;
+    return CSLS_OK;
 }
 
 // Column tiles per CTA: the split of each row tile's columns that minimises the waves of
@@ -799,8 +846,10 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     if (emu_bytes < qr_emu_scratch_bytes(s, n)) return CSLS_ERR_WORKSPACE;
     Carve c{(char*)emu_work, 0, emu_bytes, false};
     EmuScratch e = emu_carve(c, s, n);
-    // the update's bulk copies read C columns from 16-byte boundaries
+    // the update's tensor copies read C from 16-byte boundaries
     if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda & 1) != 0) return CSLS_ERR_ARG;
+    CUtensorMap cmap;
+    CSLS_TRY(make_c_map(&cmap, A, lda, s, n));
     static bool attr = false;
     if (!attr) {
         CSLS_CUDA(cudaFuncSetAttribute(k_emu_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(VtcSmem)));
@@ -899,8 +948,8 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         const int64_t nrt = ceil_div(L, kTcM), nct = ceil_div(nprime, kTcN);
         const int cpt = tc_update_cpt(nrt, nct, sms);
         k_emu_update_tc<<<dim3((unsigned)ceil_div(nct, cpt), (unsigned)nrt), kTcThreads, sizeof(TcUpdSmem), st>>>(
-            reinterpret_cast<long long*>(A), lda, s, J0, nbo, e.Vd, ldvp / kTcM, e.frow, e.Wd, ldwp / kTcN, e.gcol, e.E,
-            nprime, cpt, spin, err);
+            cmap, reinterpret_cast<long long*>(A), lda, s, J0, nbo, e.Vd, e.frow, e.Wd, e.gcol, e.E, nprime, cpt, spin,
+            err);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
         nl += 7;
