@@ -655,8 +655,7 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
             bool issued = false;
             if (tc::mbar_wait(&sm.full_a, 0, spin, kTcWaitNs, abort)) {
                 const uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
-                const uint32_t a0 = tc::smem_addr(sm.A[0]);
-                const int ksteps = (nbo + 15) >> 4;   // digit columns past nbo are zero
+                const uint64_t adesc = tc::smem_desc(tc::smem_addr(sm.A[0]), kTcM * 16, 128);
                 for (int i = 0; i < ntile; ++i) {
                     const int b = i & 1, u = i >> 1;
                     // the accumulator set of this stage was drained by the epilogue of tile i - 2
@@ -667,17 +666,21 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t b0 = tc::smem_addr(sm.B[b][0]);
+                    const uint64_t bdesc = tc::smem_desc(tc::smem_addr(sm.B[b][0]), kTcN * 16, 128);
                     const uint32_t d0 = tmem + (uint32_t)(b * kTcBufCols);
+                    // 84 MMAs, fully unrolled: each descriptor is the stage's base plus a constant
+                    // (the start address sits in the low bits, in 16-byte units); a K step of 16 is
+                    // two core-matrix columns
+#pragma unroll
                     for (int l = 0; l <= kLev; ++l)
+#pragma unroll
                         for (int p = 0; p <= l; ++p)
-                            for (int k = 0; k < ksteps; ++k) {
-                                // K step of 16 = two core-matrix columns
-                                const uint64_t ad = tc::smem_desc(a0 + p * kTcPlaneA + k * 2 * (kTcM * 16), kTcM * 16, 128);
-                                const uint64_t bd =
-                                    tc::smem_desc(b0 + (l - p) * kTcPlaneB + k * 2 * (kTcN * 16), kTcN * 16, 128);
-                                tc::mma_bf16(d0 + l * kTcN, ad, bd, idesc, (p | k) != 0);
-                            }
+#pragma unroll
+                            for (int k = 0; k < kOB / 16; ++k)
+                                tc::mma_bf16(d0 + l * kTcN,
+                                             adesc + (uint64_t)((p * kTcPlaneA + k * 2 * (kTcM * 16)) >> 4),
+                                             bdesc + (uint64_t)(((l - p) * kTcPlaneB + k * 2 * (kTcN * 16)) >> 4),
+                                             idesc, (p | k) != 0);
                     tc::mma_commit(&sm.done[b]);
                     issued = true;
                 }
@@ -944,6 +947,9 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 256)), 256, 0, st>>>(e.Wn, nbo, nprime, ldwp, e.Wd,
                                                                                         e.gcol);
         CSLS_CUDA(cudaGetLastError());
+        // a trailing block exists only right of a full 64-column outer block: the update's
+        // products always run over K = 64
+        if (nbo != kOB) return CSLS_ERR_ARG;
         tk = kt_begin(kFamUpdate, st);
         const int64_t nrt = ceil_div(L, kTcM), nct = ceil_div(nprime, kTcN);
         const int cpt = tc_update_cpt(nrt, nct, sms);
