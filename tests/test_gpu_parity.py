@@ -368,6 +368,19 @@ def test_emulated_factor_matches_oracle_well_conditioned(csls):
     assert np.all(np.diag(Re) >= 0) and np.all(np.tril(Re, -1) == 0)
 
 
+@pytest.mark.parametrize("m,n,s", [(1001, 300, 1001), (3000, 200, 799)])
+def test_emulated_factor_odd_sketch_height(csls, m, n, s):
+    # an odd number of sketch rows: the last 128-row tile of every trailing update runs past s, and
+    # 64-column outer blocks leave ragged 32-column tiles
+    rng = np.random.default_rng(m + n)
+    A = random_sparse(m, n, 12, rng)
+    R = csls.csls_factor(dev(csls, A), s=s, seed=13, prec="f64emu").R().cpu().numpy()
+    h, d = oracle.hash_rows(m, s, 13)
+    SA = oracle.sketch(A, s, h, d)
+    assert np.linalg.norm(R.T @ R - SA.T @ SA) / np.linalg.norm(SA) ** 2 < 1e-11
+    assert np.all(np.diag(R) >= 0) and np.all(np.tril(R, -1) == 0)
+
+
 @pytest.mark.parametrize("case", ["cfg1", "ragged_rfm"])
 def test_emulated_factor_rfm_backward_error_and_solve(csls, case):
     p = SKETCH_CASES[case]()
