@@ -59,3 +59,54 @@ def test_argument_errors_without_gpu(lib):
     ok = csls.csls_csr(100, 10, 0, 8, 0, 0)
     assert L.csls_factor_workspace(ctypes.byref(ok), ctypes.byref(o), ctypes.byref(pb), ctypes.byref(tb)) == 0
     assert pb.value > 10 * 10 * 8 and tb.value > 40 * 10 * 8
+
+
+def _prototypes():
+    """name -> (return type text, parameter list) for every function csls.h declares."""
+    src = open(os.path.join(ROOT, "include", "csls.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#.*", "", src)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(csls_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = " ".join(params.split())
+        plist = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        out[name] = (" ".join(ret.split()), plist)
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Each ctypes prototype has the header's parameter count, and pointer, double and integer-width kinds line up."""
+    from paper_2409_15818_gb300 import csls
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+
+    def kind_of_c(t):
+        t = t.replace("const ", "")
+        if "*" in t or t.startswith("csls_stream_t"):
+            return "ptr"
+        if t.startswith("double"):
+            return "double"
+        if t.startswith(("int64_t", "uint64_t", "size_t")):
+            return "int8B"
+        if t.startswith(("int ", "int32_t", "uint32_t")):
+            return "int4B"
+        raise AssertionError("unclassified parameter type: " + t)
+
+    def kind_of_ctypes(c):
+        if c in (ctypes.c_void_p, ctypes.c_char_p):
+            return "ptr"
+        if c is ctypes.c_double:
+            return "double"
+        return "int%dB" % ctypes.sizeof(c)
+
+    for name, (ret, params) in protos.items():
+        res, args = csls.EXPORTS[name]
+        assert len(args) == len(params), (name, len(args), params)
+        for c_type, a in zip(params, args):
+            assert kind_of_ctypes(a) == kind_of_c(c_type), (name, c_type, a)
+        if ret == "void":
+            assert res is None, name
+        elif "char" in ret:
+            assert res is ctypes.c_char_p, name
+        else:
+            assert res is ctypes.c_int, (name, ret)
