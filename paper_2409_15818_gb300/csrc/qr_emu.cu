@@ -49,14 +49,20 @@ __device__ __forceinline__ int exp_of(double amax) {
     return amax > 0.0 ? ilogb(amax) + 1 : 0;
 }
 
+// Balanced base-256 digits of |N| < 2^47: N = sum_q d[q] 256^(5 - q), d[1..5] in [-128, 127], d[0] in
+// [-128, 128]. Adding 128 to each of the five low bytes (0x8080808080) removes the borrow chain of digit
+// by digit extraction: each low digit is then a plain byte of the sum minus 128, and the top digit is the
+// sum shifted right by 40 (arithmetic).
 __device__ __forceinline__ void cut_digits(long long N, int (&d)[kDig]) {
-#pragma unroll
-    for (int q = kDig - 1; q >= 1; --q) {
-        const int r = (int)(((N + 128) & 255) - 128);
-        d[q] = r;
-        N = (N - r) >> 8;
-    }
-    d[0] = (int)N;
+    const long long M = N + 0x8080808080LL;
+    const unsigned lo = (unsigned)M;
+    const int hi = (int)(M >> 32);
+    d[5] = (int)(lo & 255u) - 128;
+    d[4] = (int)((lo >> 8) & 255u) - 128;
+    d[3] = (int)((lo >> 16) & 255u) - 128;
+    d[2] = (int)(lo >> 24) - 128;
+    d[1] = (hi & 255) - 128;
+    d[0] = hi >> 8;
 }
 
 // digits of x relative to scale 2^e (|x| < 2^e)
