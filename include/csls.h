@@ -144,9 +144,11 @@ int csls_sketch(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA,
 
 /* Same result as csls_sketch, for callers that cannot call cudaMalloc
  * themselves -- for example code whose device memory is entirely owned by
- * another framework's pool allocator, or latency-critical paths where the
- * implicit device synchronisation of cudaMalloc is not acceptable. (The paper
- * has no counterpart; this is a library convenience.)
+ * another framework's pool allocator, or a plug-in that the host application
+ * forbids to allocate device memory after start-up. (The paper has no
+ * counterpart; this is a library convenience.) Like csls_sketch, every call
+ * first validates the CSR arrays and reads the result back to the host, so it
+ * synchronises `stream` before it returns.
  * Instead of a caller workspace it uses a fixed 16 MiB scratch array that the
  * library keeps in device memory: every GPU that loads the library holds those
  * 16 MiB until the process exits. The call allocates nothing. Sizes whose

@@ -19,12 +19,12 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the oracle with gcc (-O2 -ffp-contract=off); returns the .so path."""
+    """Compile the oracle with gcc (-O2 -ffp-contract=off -fopenmp); returns the .so path."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -35,6 +35,7 @@ def _load():
         _lib = ctypes.CDLL(build())
         u64, i64, i32, dbl, vp = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
         sig = {
+            "orc_set_threads": (ctypes.c_int, [ctypes.c_int]),
             "orc_splitmix64_mix": (u64, [u64]),
             "orc_splitmix64_output": (u64, [u64, u64]),
             "orc_hash": (None, [i64, i64, u64, vp, vp]),
@@ -71,6 +72,11 @@ def _csr(A):
 
 
 # --------------------------------------------------------------------------- primitives
+
+def set_threads(nthreads):
+    """Threads of the Householder QR's column loop (results do not depend on it); returns the count."""
+    return int(_load().orc_set_threads(int(nthreads)))
+
 
 def splitmix64_output(seed, i):
     return int(_load().orc_splitmix64_output(seed, i))

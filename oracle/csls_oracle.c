@@ -10,6 +10,12 @@
  * compiled with -O2 -ffp-contract=off so no fused multiply-add changes rounding.
  * Matrices are column-major with an explicit leading dimension.
  *
+ * Threads: the one OpenMP loop is the Householder QR's loop over trailing
+ * columns. Each column's dot product and update are computed by one thread in
+ * the same order as the serial loop, so the result is bit-identical for any
+ * thread count (tested); threads only let the bench-size factorisations finish
+ * on a multi-core host.
+ *
  * Parity status: every function here is pinned by a CPU test (worked example,
  * closed form, library special case, brute force or invariant); none is
  * "parity unpinned".
@@ -18,6 +24,21 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Number of threads of the QR's column loop (no effect in a build without OpenMP);
+ * returns the count in force. */
+int orc_set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Count-sketch hash (Definition 2.3). The paper only asks that h(i) be uniform
@@ -99,6 +120,8 @@ void orc_householder_qr(int64_t s, int64_t n, double* A, int64_t lda, double* ta
         double scal = 1.0 / (alpha - beta);
         for (int64_t i = 1; i < len; ++i) x[i] *= scal;
         x[0] = beta;
+        /* columns are independent: one thread per column, same arithmetic as serially */
+#pragma omp parallel for schedule(static) if ((n - j) * len > 262144)
         for (int64_t c = j + 1; c < n; ++c) {
             double* y = A + j + c * lda;
             double w = y[0];

@@ -128,7 +128,10 @@ struct Carve {
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
-int device_sm_count();
+int device_sm_count();   // of the current device (cached per device)
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current device, once per
+// (kernel, device) pair (the attribute is per device); thread-safe.
+int raise_smem_limit(const void* kernel, int bytes);
 
 // Optional per-family kernel timing for the factorisation: while timing is on for the
 // calling thread, launch sites bracket their kernels with events on the launching

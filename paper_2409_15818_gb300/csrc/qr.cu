@@ -656,13 +656,8 @@ static int qr_factor_impl(T* A, int64_t lda, int64_t s, int64_t n, const QrScrat
     T* tau = reinterpret_cast<T*>(q.tau);
     T* Tm = reinterpret_cast<T*>(q.T);
     T* part = reinterpret_cast<T*>(q.partials);
-    static bool attr_set[2] = {false, false};
-    const int which = sizeof(T) == 8 ? 0 : 1;
     const size_t smem_cap = 200 * 1024;
-    if (!attr_set[which]) {
-        CSLS_CUDA(cudaFuncSetAttribute(k_panel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
-        attr_set[which] = true;
-    }
+    CSLS_TRY(raise_smem_limit((const void*)k_panel<T, true>, (int)smem_cap));
     int64_t nl = 0;
     for (int64_t j0 = 0; j0 < n; j0 += kPanel) {
         const int nbw = (int)(n - j0 < kPanel ? n - j0 : kPanel);
@@ -698,13 +693,8 @@ int qr_trailing_update_f64(double* A, int64_t lda, int64_t s, int64_t n_end, int
 
 int qr_panel_launch_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, const QrScratch& q, int* err,
                         long long spin, cudaStream_t st) {
-    static bool attr_set = false;
     const size_t smem_cap = 200 * 1024;
-    if (!attr_set) {
-        CSLS_CUDA(cudaFuncSetAttribute(k_panel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_cap));
-        attr_set = true;
-    }
+    CSLS_TRY(raise_smem_limit((const void*)k_panel<double, true>, (int)smem_cap));
     const int64_t L = s - j0;
     int G = panel_grid(L);
     int64_t chunk = ceil_div(L, G);

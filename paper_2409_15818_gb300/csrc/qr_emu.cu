@@ -53,6 +53,7 @@ __device__ __forceinline__ int exp_of(double amax) {
 // [-128, 128]. Adding 128 to each of the five low bytes (0x8080808080) removes the borrow chain of digit
 // by digit extraction: each low digit is then a plain byte of the sum minus 128, and the top digit is the
 // sum shifted right by 40 (arithmetic).
+static_assert(kDig == 6 && kNumBits == 47, "cut_digits is written for six digits of a 47-bit integer");
 __device__ __forceinline__ void cut_digits(long long N, int (&d)[kDig]) {
     const long long M = N + 0x8080808080LL;
     const unsigned lo = (unsigned)M;
@@ -567,6 +568,7 @@ constexpr int kTcTmemCols = 512;
 constexpr int kTcEpiWarps = 8;
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
 constexpr unsigned long long kTcWaitNs = 2000000000ULL;
+constexpr long long kTeardownSpin = 1LL << 62;   // teardown waits: bounded by kTcWaitNs alone
 
 struct TcUpdSmem {
     unsigned char A[kDig][kTcPlaneA];
@@ -644,15 +646,17 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                 if (b) armed1 = u + 1;
                 else armed0 = u + 1;
             }
-            // copies in flight land before the CTA can leave
-            tc::mbar_wait(&sm.full_a, 0, spin, kTcWaitNs, nullptr);
+            // copies in flight land before the CTA can leave. Issued copies always complete, so
+            // these waits are bounded by wall time only (not by the caller's spin count, which
+            // may be tiny): a CTA never exits with a copy still writing its shared memory.
+            tc::mbar_wait(&sm.full_a, 0, kTeardownSpin, kTcWaitNs, nullptr);
             if (armed0) {
-                tc::mbar_wait(&sm.full_b[0], (armed0 - 1) & 1, spin, kTcWaitNs, nullptr);
-                tc::mbar_wait(&sm.full_c[0], (armed0 - 1) & 1, spin, kTcWaitNs, nullptr);
+                tc::mbar_wait(&sm.full_b[0], (armed0 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
+                tc::mbar_wait(&sm.full_c[0], (armed0 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
             }
             if (armed1) {
-                tc::mbar_wait(&sm.full_b[1], (armed1 - 1) & 1, spin, kTcWaitNs, nullptr);
-                tc::mbar_wait(&sm.full_c[1], (armed1 - 1) & 1, spin, kTcWaitNs, nullptr);
+                tc::mbar_wait(&sm.full_b[1], (armed1 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
+                tc::mbar_wait(&sm.full_c[1], (armed1 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
             }
         }
         __syncwarp();
@@ -694,9 +698,9 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                 *abort = 1;
                 set_error(err, CSLS_ERR_TIMEOUT);
             }
-            if (issued) {   // every MMA has completed before the tensor memory is freed
+            if (issued) {   // every MMA has completed before the tensor memory is freed (wall-time bound only)
                 tc::mma_commit(&sm.drain);
-                tc::mbar_wait(&sm.drain, 0, spin, kTcWaitNs, nullptr);
+                tc::mbar_wait(&sm.drain, 0, kTeardownSpin, kTcWaitNs, nullptr);
             }
         }
         __syncwarp();
@@ -859,14 +863,9 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda & 1) != 0) return CSLS_ERR_ARG;
     CUtensorMap cmap;
     CSLS_TRY(make_c_map(&cmap, A, lda, s, n));
-    static bool attr = false;
-    if (!attr) {
-        CSLS_CUDA(cudaFuncSetAttribute(k_emu_vtc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(VtcSmem)));
-        CSLS_CUDA(cudaFuncSetAttribute(k_emu_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(TcUpdSmem)));
-        CSLS_CUDA(cudaFuncSetAttribute(k_wreduce_ob, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWrSmem));
-        attr = true;
-    }
+    CSLS_TRY(raise_smem_limit((const void*)k_emu_vtc, (int)sizeof(VtcSmem)));
+    CSLS_TRY(raise_smem_limit((const void*)k_emu_update_tc, (int)sizeof(TcUpdSmem)));
+    CSLS_TRY(raise_smem_limit((const void*)k_wreduce_ob, (int)kWrSmem));
     const int sms = device_sm_count();
     CSLS_CUDA(cudaMemsetAsync(q.bar, 0, sizeof(GridBarrier), st));
     k_col_exponent<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, st>>>(A, lda, s, n, e.E);

@@ -146,10 +146,10 @@ int sketch_run(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA, 
     CSLS_TRY(scan_counts(sc.counts, sc.offsets, s, st));
     k_hash_scatter<<<grid_cap(m, 256), 256, 0, st>>>(m, (uint32_t)s, seed, sc.offsets, sc.cursor, sc.list);
     CSLS_CUDA(cudaGetLastError());
-    // Bucket sizes are Poisson(m/s); the CTA sort covers buckets up to 4096 rows and the
-    // global-memory fallback any longer one, so the hint is only an upper estimate.
-    int64_t hint = m / (s > 0 ? s : 1) * 4 + 64;
-    CSLS_TRY(segmented_sort(sc.list, nullptr, sc.offsets, s, hint > m ? m : hint, st));
+    // Bucket sizes are Poisson(m/s), but nothing bounds the longest one on the host side, so
+    // all three sort stages are launched (each returns at once for segments outside its size
+    // range): every bucket ends up in ascending row order whatever its length.
+    CSLS_TRY(segmented_sort(sc.list, nullptr, sc.offsets, s, m, st));
     const int esz = prec == CSLS_PREC_F64 ? 8 : 4;
     if (ld == s && esz == 8 && ((uintptr_t)SA % 16) == 0 && (s * n) % 2 == 0) {
         k_zero_vec<<<grid_cap(s * n / 2, 256), 256, 0, st>>>((double2*)SA, s * n / 2);

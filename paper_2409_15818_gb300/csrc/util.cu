@@ -3,19 +3,41 @@
 
 #include <vector>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "csls_internal.cuh"
 
 namespace csls {
 
+namespace {
+constexpr int kMaxDev = 64;
+std::mutex g_dev_mu;
+int g_sm_count[kMaxDev] = {};
+std::set<std::pair<const void*, int>> g_smem_attr_done;   // (kernel, device) pairs already raised
+}  // namespace
+
 int device_sm_count() {
-    static int cached = 0;
-    if (cached == 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (g_sm_count[dev] == 0) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-        cached = v > 0 ? v : 1;
+        g_sm_count[dev] = v > 0 ? v : 1;
     }
-    return cached;
+    return g_sm_count[dev];
+}
+
+int raise_smem_limit(const void* kernel, int bytes) {
+    int dev = 0;
+    CSLS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    const auto key = std::make_pair(kernel, dev);
+    if (g_smem_attr_done.count(key)) return CSLS_OK;
+    CSLS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    g_smem_attr_done.insert(key);
+    return CSLS_OK;
 }
 
 // ------------------------------------------------------------------ per-family kernel timing
@@ -180,6 +202,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_big(int32_t* keys, int32_
     }
 }
 
+// max_hint must bound the longest segment from above (stages for longer segments are skipped).
 int segmented_sort(int32_t* keys, int32_t* payload, const int64_t* off, int64_t nseg, int64_t max_hint,
                    cudaStream_t st) {
     if (nseg <= 0) return CSLS_OK;

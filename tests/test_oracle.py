@@ -458,3 +458,16 @@ def test_explicit_form_solution_matches_direct_and_implicit():
     b = rng.standard_normal(60)
     x1, _, _ = oracle.explicit_lsqr(A, b, dict(kind="qr", R=np.eye(5), F=np.eye(5)), tol=1e-15, maxit=50)
     np.testing.assert_allclose(x1, np.linalg.lstsq(A.dense(), b, rcond=None)[0], rtol=1e-10, atol=1e-12)
+
+
+def test_threaded_qr_is_bit_identical():
+    """The oracle's one OpenMP loop (trailing columns of the Householder QR) leaves every column's
+    arithmetic in the serial order, so any thread count gives the same bits."""
+    M = np.random.default_rng(3).standard_normal((700, 300))
+    prev = oracle.set_threads(0)
+    oracle.set_threads(1)
+    F1, t1 = oracle.householder_qr(M)
+    oracle.set_threads(4)
+    F4, t4 = oracle.householder_qr(M)
+    oracle.set_threads(prev)
+    assert np.array_equal(F1, F4) and np.array_equal(t1, t4)

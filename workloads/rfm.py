@@ -17,6 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .rng import splitmix_uniform
+from . import detmath
 
 _STREAM_FEATURES = 0x5EA7
 
@@ -91,9 +92,9 @@ def _rhs_f(pts, modes):
     """-Laplace of prod sin(a_d pi x_d) = pi^2 (sum a_d^2) prod sin(a_d pi x_d)."""
     out = np.empty((len(modes), pts.shape[0]))
     for r, mode in enumerate(modes):
-        val = np.full(pts.shape[0], np.pi ** 2 * float(sum(a * a for a in mode)))
+        val = np.full(pts.shape[0], np.pi * np.pi * float(sum(a * a for a in mode)))
         for d, a in enumerate(mode):
-            val *= np.sin(a * np.pi * pts[:, d])
+            val *= detmath.sin(a * np.pi * pts[:, d])
         out[r] = val
     return out
 
@@ -103,7 +104,7 @@ def _exact_vals(pts, modes):
     for r, mode in enumerate(modes):
         val = np.ones(pts.shape[0])
         for d, a in enumerate(mode):
-            val *= np.sin(a * np.pi * pts[:, d])
+            val *= detmath.sin(a * np.pi * pts[:, d])
         out[r] = val
     return out
 
@@ -148,7 +149,7 @@ def _assemble(grid, J, q, e_bc, e_if, R, seed, modes):
     n = n_boxes * J
     k, c = _features(seed, n_boxes, J, dim, R)
     r = 0.5 / np.asarray(grid, dtype=np.float64)
-    inv_r2 = 1.0 / r ** 2
+    inv_r2 = 1.0 / (r * r)
     asm = _Assembler(len(modes))
     boxes = [tuple(int(v) for v in np.unravel_index(b, grid[::-1])[::-1]) for b in range(n_boxes)]
 
@@ -163,8 +164,13 @@ def _assemble(grid, J, q, e_bc, e_if, R, seed, modes):
         return np.stack([m.reshape(-1) for m in mesh[::-1]], axis=1)
 
     def phi_parts(box, t):
-        z = t @ k[box].T + c[box]
-        th = np.tanh(z)
+        # z = k . t + c summed in axis order with elementwise IEEE operations (no BLAS), and tanh from
+        # detmath, so the matrix is bit-identical on every machine
+        z = t[:, 0:1] * k[box][None, :, 0]
+        for d in range(1, dim):
+            z = z + t[:, d:d + 1] * k[box][None, :, d]
+        z = z + c[box][None, :]
+        th = detmath.tanh(z)
         return th, 1.0 - th * th
 
     # PDE rows: -Laplace u_n = f
@@ -172,7 +178,9 @@ def _assemble(grid, J, q, e_bc, e_if, R, seed, modes):
     for box in range(n_boxes):
         centre = (2 * np.asarray(boxes[box]) + 1) * r
         th, sech2 = phi_parts(box, t_in)
-        lap_scale = (k[box] ** 2) @ inv_r2          # (J,)
+        lap_scale = k[box][:, 0] * k[box][:, 0] * inv_r2[0]   # (J,): sum_d k_d^2 / r_d^2
+        for d in range(1, dim):
+            lap_scale = lap_scale + k[box][:, d] * k[box][:, d] * inv_r2[d]
         vals = 2.0 * th * sech2 * lap_scale[None, :]  # -tanh''(z) * sum k_d^2 / r_d^2
         pts = centre + t_in * r
         asm.add(vals, box * J + np.arange(J), _rhs_f(pts, modes))

@@ -8,6 +8,8 @@ coincide with the hash that the solver derives from its own seed.
 """
 import numpy as np
 
+from . import detmath
+
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
@@ -45,4 +47,4 @@ def splitmix_normal(seed, stream, count, offset=0):
     u = splitmix_uniform(seed, stream, 2 * count, 2 * offset)
     u1 = 1.0 - u[0::2]  # in (0, 1]
     u2 = u[1::2]
-    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return np.sqrt(-2.0 * detmath.log(u1)) * detmath.cos(2.0 * np.pi * u2)

@@ -10,6 +10,7 @@ import numpy as np
 
 from .rng import splitmix_uniform, splitmix_normal, splitmix_bits
 from .rfm import RFMProblem, poisson2d, poisson3d
+from . import detmath
 
 _STREAM_COLS = 0xC015
 _STREAM_VALS = 0x7A15
@@ -57,7 +58,7 @@ def scaled_random_sparse(m, n, per_row=10, cond_exp=10.0, noise=1e-8, seed=5):
         dup = np.any(draw[:, 1:] == draw[:, :-1], axis=1) if per_row > 1 else np.zeros(todo.size, bool)
         todo = todo[dup]
         attempt += 1
-    scale = 10.0 ** (-cond_exp * np.arange(n) / max(n - 1, 1))
+    scale = detmath.pow10(-cond_exp * np.arange(n) / max(n - 1, 1))
     vals = splitmix_normal(seed, _STREAM_VALS, m * per_row).reshape(m, per_row) * scale[cols]
     x_true = splitmix_normal(seed, _STREAM_XTRUE, n)
     rows = np.repeat(np.arange(m), per_row)
