@@ -157,6 +157,23 @@ def replica_problem(config, rank):
     return config_problem(config)
 
 
+# ncu DRAM traffic per launch of the dominant factor kernels (dram__bytes_read.sum + dram__bytes_write.sum),
+# from the captures summarised under profiles/; None until a capture of the current kernel exists.
+TRAFFIC = {}
+TRAFFIC_SOURCE = None
+
+
+def oracle_cache(p, config):
+    """The oracle's cached solutions of this workload (tests/golden/oracle_<config>.npz), if they were
+    computed for exactly these inputs (same SHA-256 of the CSR arrays and right-hand side)."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_%s.npz" % config)
+    if not os.path.exists(path):
+        return None
+    from workloads import input_hash
+    d = dict(np.load(path, allow_pickle=False))
+    return d if str(d.get("input_hash")) == input_hash(p) else None
+
+
 def qr_flops(s, n):
     return 2.0 * s * n * n - 2.0 / 3.0 * n ** 3
 
@@ -172,14 +189,15 @@ def spmv_pair_bytes(m, n, nnz):
 def oracle_sample_seconds(p, s, iters_full):
     """Time the oracle on a bounded sample of the workload and scale it to one
     full solve: the full sketch, Householder QR of the first k columns of the
-    sketch (extrapolated by flop count) and 2 LSQR iterations (scaled by the
-    iteration count the GPU solve needed)."""
+    sketch (extrapolated by flop count; the QR's column loop runs on all host
+    cores) and 2 LSQR iterations (scaled by the iteration count of the solve)."""
     import oracle
+    threads = oracle.set_threads(len(os.sched_getaffinity(0)))
     t0 = time.perf_counter()
     h, d = oracle.hash_rows(p.m, s, 1)
     SA = oracle.sketch(p, s, h, d)
     t_sketch = time.perf_counter() - t0
-    k = 160
+    k = 320
     sub = np.asfortranarray(SA[:, :k])
     t0 = time.perf_counter()
     oracle.householder_qr(sub)
@@ -191,10 +209,10 @@ def oracle_sample_seconds(p, s, iters_full):
     oracle.lsqr(p, p.b[0], R, "qr", fixed_iters=2)
     t_it = (time.perf_counter() - t0) / 2.0
     total = t_sketch + t_qr + t_it * iters_full
-    sample = ("oracle (single-thread C) on %s: full sketch %.2fs + Householder QR of the first %d of %d "
-              "sketch columns %.2fs scaled by flops to %.1fs + 2 LSQR iterations %.2fs/it x %d iterations"
-              % (WORKLOAD, t_sketch, k, p.n, t_qr_k, t_qr, t_it, iters_full))
-    return total, sample, t_sketch + t_qr_k + 2 * t_it
+    sample = ("oracle (C; the Householder column loop on %d threads) on %s: full sketch %.2fs + Householder QR "
+              "of the first %d of %d sketch columns %.2fs scaled by flops to %.1fs + 2 LSQR iterations %.2fs/it x "
+              "%d iterations" % (threads, WORKLOAD, t_sketch, k, p.n, t_qr_k, t_qr, t_it, iters_full))
+    return total, sample, t_sketch + t_qr_k + 2 * t_it, threads
 
 
 def run_reference(args):
@@ -206,18 +224,21 @@ def run_reference(args):
     from workloads import config_problem
     p = config_problem(args.config)
     s = 4 * p.n
-    iters = 64
+    # the oracle's own iteration count at this workload (cached oracle run), else the GPU's last count
+    cache = oracle_cache(p, args.config)
+    iters = int(cache["it_tol1"]) if cache is not None and "it_tol1" in cache else 83
     vals = []
     sample = ""
+    threads = 1
     for _ in range(args.warmup + args.steps):
-        v, sample, _ = oracle_sample_seconds(p, s, iters)
+        v, sample, _, threads = oracle_sample_seconds(p, s, iters)
         vals.append(v)
     v = statistics.median(vals[args.warmup:]) if args.steps > 0 else vals[-1]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "replicas"},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -439,6 +460,54 @@ def main():
     read_gbs = read_ceiling_gbs()
     pair_gbs = spmv_pair_bytes(m, n, nnz) / (pair_ms * 1e-3) / 1e9
 
+    # triangular-solve pair (z = R^-1 v, then R^-T z), each call timed with events on the stream
+    # (includes the call's small status memsets), and the whole LSQR iteration from the solve time
+    trsv = None
+    if args.variant == "qr":
+        v = torch.randn(n, dtype=torch.float64, device="cuda")
+        csls.csls_precond_apply(F, v)
+        tms = []
+        for _ in range(5):
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            zz = csls.csls_precond_apply(F, v)
+            csls.csls_precond_apply(F, zz, trans=True)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            tms.append(t0.elapsed_time(t1))
+        trsv_ms = statistics.median(tms)
+        trsv_bytes = 8 * n * (n + 1)   # the upper triangle of R read twice
+        trsv = {"bound": "hbm", "ms": trsv_ms, "bytes": trsv_bytes, "achieved": trsv_bytes / (trsv_ms * 1e-3) / 1e9,
+                "peak": hbm, "unit": "GB/s", "frac": trsv_bytes / (trsv_ms * 1e-3) / 1e9 / hbm,
+                "fp64_floor_ms": n * n / (152 * 2 * 2.07e9) * 1e3,
+                "fp64_floor_source": "n^2 FP64 FMAs at 2 per clock per SM (152 SMs, 2.07 GHz)"}
+    it_bytes = spmv_pair_bytes(m, n, nnz) + 8 * n * (n + 1) + 48 * m + 64 * n
+    it_ms = statistics.median(solve_ms) / max(1, int(statistics.median(iters)))
+    iteration = {"ms": it_ms, "bytes": it_bytes, "achieved": it_bytes / (it_ms * 1e-3) / 1e9, "peak": hbm,
+                 "unit": "GB/s", "frac": it_bytes / (it_ms * 1e-3) / 1e9 / hbm,
+                 "bytes_source": "SpMV pair 2 (12 nnz) + 8 (m + 1) + 8 (n + 1) + 16 (m + n), TRSV pair 8 n (n + 1), "
+                                 "vectors 48 m + 64 n"}
+    # A-norm error against the oracle's cached solutions of these exact inputs (Theorem 3.3's norm)
+    accuracy = None
+    cache = oracle_cache(p, args.config) if args.variant == "qr" and not args.explicit else None
+    if cache is not None:
+        Ap = torch.sparse_csr_tensor(A.row_ptr, A.col.to(torch.int64), A.val, (m, n))
+        def anorm(xa, ref):
+            xa = xa.reshape(-1) if torch.is_tensor(xa) else torch.tensor(xa, device="cuda")
+            r = torch.tensor(ref, device="cuda")
+            return float(torch.linalg.vector_norm(Ap @ (xa - r).unsqueeze(1)) /
+                         torch.linalg.vector_norm(Ap @ r.unsqueeze(1)))
+        accuracy = {"rel_err_A_vs_oracle_floor": anorm(x, cache["x_floor1"]),
+                    "rel_err_A_vs_oracle_tol": anorm(x, cache["x_tol1"]),
+                    "oracle_iterations": int(cache["it_tol1"]),
+                    "reference": "oracle CSQRP-LSQR (same sketch seed) run 250 iterations to the floating-point floor; "
+                                 "tol run = the same stopping rule as this solve (tests/golden/oracle_%s.npz)"
+                                 % args.config}
+        if "x_floor2" in cache:   # the problem's own spread: two sketches, each at the oracle's floor
+            accuracy["oracle_spread_A"] = anorm(cache["x_floor2"], cache["x_floor1"])
+        if "x_hh" in cache:       # the dense Householder direct solve against the implicit form's floor
+            accuracy["oracle_hhqr_vs_floor_A"] = anorm(cache["x_hh"], cache["x_floor1"])
+
     # end to end through the public API with host buffers
     h_row = torch.tensor(p.row_ptr).pin_memory()
     h_col = torch.tensor(p.col).pin_memory()
@@ -490,7 +559,8 @@ def main():
     # W = V^T C, C -= V W), the one with the most device time over the timed steps, its CUDA-event
     # time summed over its launches (algorithmic flops per launch / average launch time)
     qr_gflops = qr_flops(s, n) / (statistics.median(qr_ms) * 1e-3) / 1e9
-    fam_names = {"f64emu": ["k_panel (FP64 Householder panel)", "k_emu_vtc (W = V^T C, exact bf16 digit products)",
+    fam_names = {"f64emu": ["k_obpanel (FP64 Householder outer-block panel, T and V digits)",
+                            "k_emu_vtc_tc (W = V^T C, exact bf16 digit products on tcgen05)",
                             "k_emu_update_tc (C -= V W, exact bf16 digit products on tcgen05)"],
                  "f64": ["k_panel (FP64 Householder panel)", "k_vtc_f64 (W = V^T C, DMMA)",
                          "k_update_f64 (C -= V W, DMMA)"],
@@ -507,11 +577,10 @@ def main():
         pairs = 21
         ach = pairs * kern_flop[top] / top_s / 1e12
         peak = bf16_sus
-        traffic = None   # no ncu capture of the current dominant kernels yet
+        traffic = TRAFFIC.get(fam_names[top].split(" ")[0])
         roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": peak,
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on a smaller "
-                                      "case, scaled per unit (profiles/emu_update64_rfm6x6.md)" if traffic else None,
+                    "traffic_source": TRAFFIC_SOURCE if traffic else None,
                     "peak_source": src + " bf16 sustained (kernel timed inside a multi-second step)",
                     "fp64_equivalent_tflops": kern_flop[top] / top_s / 1e12, "launches": kern_n[top],
                     "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
@@ -533,15 +602,16 @@ def main():
     roofline["qr_fp64_equivalent_tflops"] = qr_gflops / 1e3
     cpu = None
     if rank == 0:
-        total, sample, spent = oracle_sample_seconds(p, s, int(statistics.median(iters)))
-        cpu = {"value": total, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+        total, sample, spent, threads = oracle_sample_seconds(p, s, int(statistics.median(iters)))
+        cpu = {"value": total, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample}
     if rank == 0:
         line = {
             "metric": METRIC, "value": ms / 1e3 / world, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None,
             "dtype": {"f64": "f64", "f32": "f32 factor / f64 LSQR",
-                      "f64emu": "f64 (trailing-update products from exact bf16 digit products)"}[args.prec],
+                      "f64emu": "f64 LSQR; factor panels f64, trailing products emulated from bf16 digit products "
+                                "(47-bit operands, relative error ~2^-38)"}[args.prec],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": nnz, "s": s, "tol": 1e-12,
                        "variant": args.variant, "start": "R^-1 Q^T S b" if args.warm else "0",
@@ -553,6 +623,10 @@ def main():
                          "solve": statistics.median(solve_ms),
                          **({"form_b": rep.get("ms_form_b")} if args.explicit else {})},
             "roofline": roofline,
+            "cond_est": rep.get("cond_est"),
+            "accuracy": accuracy,
+            "trsv_pair": trsv,
+            "iteration": iteration,
             "spmv_pair": {"bound": "hbm", "achieved": pair_gbs, "peak": hbm, "unit": "GB/s", "frac": pair_gbs / hbm,
                           "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src + " copy (read + write)",
                           "read_only_ceiling": read_gbs, "frac_of_read_ceiling": pair_gbs / read_gbs,

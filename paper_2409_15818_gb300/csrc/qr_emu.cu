@@ -1,7 +1,7 @@
 // Blocked Householder QR of the sketch with the trailing-matrix products done on
 // the bf16 tensor cores at FP64-level accuracy (Algorithm 1 step 3).
 //
-// GB300 runs FP64 MMA at ~1.1 TFLOP/s but bf16 mma.sync at ~600 TFLOP/s, so the two
+// GB300 runs FP64 arithmetic at ~1.1 TFLOP/s but bf16 tcgen05 MMA at ~1.7 PFLOP/s, so the two
 // products of every trailing update (W = V^T C and C += V Wn) are computed from
 // exact integer pieces, in the spirit of Ozaki, Ogita, Oishi and Rump's
 // error-free splitting of matrix products:
@@ -9,18 +9,17 @@
 //     power-of-two scale shared along the contraction (per row of the left
 //     operand, per column of the right one) and cut into 6 balanced base-256
 //     digits in [-128, 128], each exact in bf16;
-//   * digit-plane products are exact integers below 2^14, and a sum of at most
-//     6 x 32 of them stays below 2^22, so the FP32 accumulation of mma.sync
-//     (started from 1.5 * 2^23, where the float grid is the integers) is exact; digit pairs of the same weight (level l = p + q) share one
-//     accumulator; levels 0..5 are kept (21 of 36 pairs), the dropped ones weigh
-//     2^-48 of the leading term;
+//   * digit-plane products are exact integers of at most 2^14; digit pairs of the
+//     same weight (level l = p + q) share one FP32 accumulator in tensor memory, and
+//     every level sum is kept below 2^24 so the FP32 accumulation is exact; levels
+//     0..5 are kept (21 of 36 pairs), the dropped ones weigh 2^-48 of the leading term;
 //   * levels are combined in int64.
 // The trailing matrix is held in int64 fixed point per column: value =
 // Cfix * 2^(E_c - 62) with 2^E_c above the column's 2-norm. Orthogonal updates
 // never increase the norm of a trailing column, so the scale is fixed for the
 // whole factorisation and C += V Wn is an exact integer addition -- the update
 // never touches the FP64 pipe. A column switches to FP64 (in place, same bytes)
-// when it becomes part of a panel; the panel is factored in FP64 by k_panel.
+// when it becomes part of a panel; the panel is factored in FP64 by k_obpanel.
 #include <algorithm>
 
 #include <cuda.h>
@@ -35,12 +34,10 @@ constexpr int kDig = 6;          // digits per operand
 constexpr int kLev = 5;          // highest kept level p + q
 constexpr int kFixBits = 62;     // fixed-point fraction bits of the trailing matrix
 constexpr int kNumBits = 8 * kDig - 1;   // integer bits of an operand before cutting into digits (47)
-constexpr int kVtcStep = 32;     // rows per exact FP32 accumulation in W = V^T C
 // FP32 accumulators start at 1.5 * 2^23: while |sum| < 2^22 the integer sum sits exactly in the
 // low mantissa bits, so it is read back with one integer subtraction (no conversion instruction).
 constexpr float kMagic = 12582912.0f;
 constexpr int kMagicBits = 0x4B400000;
-constexpr int kEmuThreads = 256;
 
 // ------------------------------------------------------------------ digit helpers
 
@@ -85,31 +82,7 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {
     return (unsigned short)(__float_as_uint(f) >> 16);
 }
 
-__device__ __forceinline__ int magic_to_int(float acc) { return __float_as_int(acc) - kMagicBits; }
-
-__device__ __forceinline__ void hmma(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
-    const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gmem), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Four 8x8 b16 matrices from shared memory in the mma.sync fragment order; `row` is this
-// lane's row address.
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* row) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(row);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // ------------------------------------------------------------------ setup kernels
 
@@ -145,125 +118,38 @@ __global__ void k_to_fixed(double* A, int64_t lda, int64_t s, int64_t n, const i
     }
 }
 
-// In place: panel columns [j0, j0 + nbw), rows [j0, s): fixed point -> double.
-__global__ void k_panel_to_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, const int* E) {
-    for (int64_t c = j0 + blockIdx.y; c < j0 + nbw; c += gridDim.y) {
-        const int sh = E[c] - kFixBits;
-        long long* colf = reinterpret_cast<long long*>(A + c * lda);
-        for (int64_t r = j0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s;
-             r += (int64_t)gridDim.x * blockDim.x)
-            A[r + c * lda] = E[c] > -1000 ? ldexp((double)colf[r], sh) : 0.0;
-    }
-}
-
-// Rows above the trailing block in the not-yet-factored columns also hold fixed point
-// (rows [0, j0) of columns >= j0 are final R entries): convert those rows of the panel too.
-__global__ void k_panel_top_to_f64(double* A, int64_t lda, int64_t j0, int nbw, const int* E) {
-    const int64_t c = j0 + blockIdx.y;
-    if (c >= j0 + nbw) return;
-    const int sh = E[c] - kFixBits;
-    long long* colf = reinterpret_cast<long long*>(A + c * lda);
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < j0; r += (int64_t)gridDim.x * blockDim.x)
-        A[r + c * lda] = E[c] > -1000 ? ldexp((double)colf[r], sh) : 0.0;
-}
-
 // ------------------------------------------------------------------ outer-block digit kernels
 //
-// The emulated products act on outer blocks of kOB = 64 columns: two 32-wide panels are
-// factored in binary64 (the second after the first one's update, on the FP64 MMA pipe),
-// their compact-WY factors are merged, and the trailing matrix is updated once per 64
-// columns. A product with K = 64 keeps every level sum below 6 x 64 x 2^14 < 2^24, so it
-// is exact in FP32 and is read back with one rounding conversion per level.
+// The emulated products act on outer blocks of kOB = 64 columns: the block is factored in
+// binary64 by one cooperative kernel (k_obpanel, which also forms the block's compact-WY T and
+// the digit planes of V), and the trailing matrix is updated once per 64 columns. A product with
+// K = 64 keeps every level sum below 6 x 64 x 2^14 < 2^24, so it is exact in FP32 and is read
+// back with one rounding conversion per level.
 
 constexpr int kOB = 2 * kPanel;   // 64
 
 // Tiles of the tcgen05 update C += V Wn: 128 rows (one TMEM lane each) x 32 columns. Its digit
-// planes are stored tile by tile (the 6 planes of a tile contiguous) in the canonical K-major
-// core-matrix order, so that one bulk copy moves a tile's planes into shared memory ready for
-// the MMA: in a V plane the 16-byte chunk holding row r, columns 8 kg .. 8 kg + 7 sits at chunk
-// index kg x 128 + r (Wn planes: kg x 32 + c).
+// planes are stored tile by tile in the canonical K-major core-matrix order, so that one bulk
+// copy moves a tile's planes into shared memory ready for the MMA. In a V plane the 16-byte
+// chunk holding row r, columns 8 kg .. 8 kg + 7 sits at chunk index kg x 128 + r. The six Wn
+// planes of a column tile are stacked along N (row q x 32 + c of a 192-row operand), chunk
+// index kg x 192 + q x 32 + c: one MMA with N = 32 (6 - p) then multiplies V plane p by Wn
+// planes 0 .. 5 - p at once, writing levels p .. 5, whose TMEM blocks are adjacent.
 constexpr int kTcM = 128;
 constexpr int kTcN = 32;
+constexpr int kTcNStack = kDig * kTcN;   // 192 rows of the stacked Wn operand
 __device__ __forceinline__ int64_t vd_chunk(int p, int64_t lr, int kg) {
     return (((lr >> 7) * kDig + p) * 8 + kg) * kTcM + (lr & (kTcM - 1));
 }
+// Column-scaled V digits for W = V^T C, in the K-major core-matrix order of that product's B operand:
+// the six planes stacked along N (row p x 64 + a), 16-byte chunks of 8 consecutive rows, chunk
+// index (lr / 8) x 384 + p x 64 + a -- so the digits of any 32 rows starting at a multiple of 32 are
+// one contiguous 24 KB block (one bulk copy).
+__device__ __forceinline__ int64_t vtd_index(int p, int a, int64_t lr) {
+    return (((lr >> 3) * (kDig * kOB) + p * kOB + a) << 3) + (lr & 7);
+}
 __device__ __forceinline__ int64_t wd_chunk(int q, int64_t c, int kg) {
-    return (((c >> 5) * kDig + q) * 8 + kg) * kTcN + (c & (kTcN - 1));
-}
-
-// Masked Householder vector entry of the outer block starting at J0: 0 above the diagonal,
-// 1 on it, the stored tail below.
-__device__ __forceinline__ double vmask(const double* A, int64_t lda, int64_t r, int64_t J0, int a) {
-    const int64_t d = J0 + a;
-    return r < d ? 0.0 : (r == d ? 1.0 : A[r + d * lda]);
-}
-
-// Column maxima of V (for the V^T C digits), as ordered bit patterns (|x| >= 0).
-__global__ void __launch_bounds__(256) k_vcolmax(const double* A, int64_t lda, int64_t s, int64_t J0, int nbo,
-                                                 unsigned long long* colmax) {
-    __shared__ unsigned long long red[kOB];
-    if (threadIdx.x < kOB) red[threadIdx.x] = 0ULL;
-    __syncthreads();
-    const int a = threadIdx.x & (kOB - 1);
-    unsigned long long best = 0ULL;
-    if (a < nbo) {
-        for (int64_t r = J0 + blockIdx.x * 4 + (threadIdx.x >> 6); r < s; r += (int64_t)gridDim.x * 4) {
-            const unsigned long long b = __double_as_longlong(fabs(vmask(A, lda, r, J0, a)));
-            best = b > best ? b : best;
-        }
-        atomicMax(&red[a], best);
-    }
-    __syncthreads();
-    if (threadIdx.x < nbo) atomicMax(&colmax[threadIdx.x], red[threadIdx.x]);
-}
-
-// Digits of V: per-row scale for C += V Wn (Vd: plane tiles of 128 rows in core-matrix order,
-// ldv a multiple of 128) and per-column scale for V^T C (VTd[p][a][r], r contiguous). Rows are
-// local row indices r - J0; columns a >= nbo and rows past the block are zero digits.
-__global__ void __launch_bounds__(256) k_vdigits(const double* A, int64_t lda, int64_t s, int64_t J0, int nbo,
-                                                 const unsigned long long* colmax, int64_t ldv,
-                                                 unsigned short* Vd, unsigned short* VTd, int* frow, int* ecol) {
-    __shared__ int ecol_s[kOB];
-    if (threadIdx.x < kOB) {
-        const int e = threadIdx.x < nbo ? exp_of(__longlong_as_double((long long)colmax[threadIdx.x])) : 0;
-        ecol_s[threadIdx.x] = e;
-        if (blockIdx.x == 0) ecol[threadIdx.x] = e;
-    }
-    __syncthreads();
-    const int64_t L = s - J0;
-    for (int64_t lr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; lr < ldv; lr += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = J0 + lr;
-        double mx = 0.0;
-        for (int a = 0; a < nbo; ++a)
-            if (lr < L) mx = fmax(mx, fabs(vmask(A, lda, r, J0, a)));
-        const int f = exp_of(mx);
-        frow[lr] = f;
-        // the row-scaled digits of 8 consecutive columns go out as one 16-byte chunk per plane
-        // (consecutive rows are consecutive chunks); the column-scaled planes are written entry by
-        // entry, consecutive across the threads
-        for (int a0 = 0; a0 < kOB; a0 += 8) {
-            uint32_t pk[kDig][4];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int a = a0 + j;
-                const double v = (lr < L && a < nbo) ? vmask(A, lda, r, J0, a) : 0.0;
-                int d[kDig], dt[kDig];
-                digits_f64(v, f, d);
-                digits_f64(v, ecol_s[a], dt);
-#pragma unroll
-                for (int p = 0; p < kDig; ++p) {
-                    const uint32_t h = bf16_of_int(d[p]);
-                    if (j & 1) pk[p][j >> 1] |= h << 16;
-                    else pk[p][j >> 1] = h;
-                    VTd[((int64_t)p * kOB + a) * ldv + lr] = bf16_of_int(dt[p]);
-                }
-            }
-#pragma unroll
-            for (int p = 0; p < kDig; ++p)
-                reinterpret_cast<uint4*>(Vd)[vd_chunk(p, lr, a0 >> 3)] =
-                    make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
-        }
-    }
+    return ((c >> 5) * 8 + kg) * kTcNStack + q * kTcN + (c & (kTcN - 1));
 }
 
 // Wn = -T^T (sum of the split-K partials of W = V^T C) for the outer block (T: nbo x nbo upper
@@ -299,16 +185,18 @@ __global__ void __launch_bounds__(256) k_wreduce_ob(const double* Wp, int ks, co
     }
 }
 
-// Digits of Wn (kOB x nprime, row-major): per-column scale; Wd in plane tiles of 32 columns in
-// core-matrix order (ldw a multiple of 32).
-__global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw, unsigned short* Wd, int* gcol) {
+// Digits of Wn (kOB x nprime, row-major): per-column scale 2^g_c; Wd in plane tiles of 32 columns in
+// core-matrix order (ldw a multiple of 32). gsh[c] = g_c - E_(jc + c) + 62 - 14 - 8 kLev is the column's
+// part of the shift that puts an update product onto the fixed-point grid of trailing column jc + c.
+__global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw, unsigned short* Wd, const int* E,
+                          int64_t jc, int* gsh) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ldw; c += (int64_t)gridDim.x * blockDim.x) {
         double mx = 0.0;
         for (int a = 0; a < nbo; ++a)
             if (c < nprime) mx = fmax(mx, fabs(Wn[(int64_t)a * nprime + c]));
         const int g = exp_of(mx);
-        gcol[c] = g;
-        for (int a0 = 0; a0 < kOB; a0 += 8) {   // 16-byte chunks, as in k_vdigits
+        gsh[c] = c < nprime ? g - E[jc + c] + kFixBits - 14 - 8 * kLev : 0;
+        for (int a0 = 0; a0 < kOB; a0 += 8) {   // 16-byte chunks of 8 K-consecutive digits
             uint32_t pk[kDig][4];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -331,214 +219,289 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
     }
 }
 
-// ------------------------------------------------------------------ merging the two panels' T
+// ------------------------------------------------------------------ fused outer-block panel
+//
+// The Householder factorisation of one outer block (nbo <= 64 columns, rows J0 .. s - 1) as one
+// cooperative launch, plus everything the emulated trailing products need from it. A CTA owns a
+// contiguous chunk of rows, converts its part of the block from fixed point to binary64 (kept in
+// shared memory when it fits) and applies every reflector to it locally. Column c needs one
+// grid-wide reduction: for x = A(j:s, j), j = J0 + c, the tail norm sigma = ||x(1:)||^2, the
+// diagonal alpha = x(0), and for every later block column k the tail product d_k = x(1:)^T A(j+1:s, k)
+// and the entry top_k = A(j, k). With beta = -sign(alpha) sqrt(alpha^2 + sigma), tau = (beta -
+// alpha) / beta and v = [1; x(1:) / (alpha - beta)], the product v^T A(j:s, k) = top_k + d_k /
+// (alpha - beta), so every CTA forms the reflector and updates its rows without a second
+// reduction. The same pass that computes the next column's sums also computes the Gram column
+// V(:, 0:c)^T v_c and the column maximum |v_c| (for T and the column-scaled digits), so the block
+// costs nbo + 1 grid barriers. Partials are summed in a fixed order (lane-strided, then a fixed
+// shuffle tree) by every CTA alike, so all CTAs hold identical bits and results are reproducible.
+// At the end CTA 0 forms T of the compact WY form (T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i)
+// V(:, 0:i)^T v_i), every CTA writes its rows of V / R back in binary64 and cuts them into the
+// row-scaled (Vd) and column-scaled (VTd) digit planes.
+constexpr int kObThreads = 512;
+constexpr int kObWarps = kObThreads / 32;
+// reduction slots: sigma, alpha, d_k (64), top_k (64), Gram column (64), column max
+constexpr int kRedSig = 0, kRedAlpha = 1, kRedD = 2, kRedTop = 2 + kOB, kRedGram = 2 + 2 * kOB,
+              kRedMax = 2 + 3 * kOB, kRedSlots = 3 + 3 * kOB;
+constexpr size_t kObSmemCap = 180 * 1024;   // dynamic part (the static part is ~41 KB of the 227 KB)
 
-// Partial Gram block G12(a, b) = V1(:, a)^T V2(:, b) over one row chunk per CTA (rows from
-// J0 + 32: V1 is zero-free below its diagonal there, V2 is masked). part[g][a + 32 b].
-__global__ void __launch_bounds__(256) k_gram12(const double* A, int64_t lda, int64_t s, int64_t J0, int nb2,
-                                                int64_t chunk, double* part) {
-    __shared__ double V1s[64][kPanel + 1];
-    __shared__ double V2s[64][kPanel + 1];
-    const int tid = threadIdx.x, a = tid & 31, bq = tid >> 5;   // outputs (a, 4 bq .. 4 bq + 3)
-    const int64_t rb = J0 + kPanel + (int64_t)blockIdx.x * chunk;
-    const int64_t re = rb + chunk < s ? rb + chunk : s;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t t0 = rb; t0 < re; t0 += 64) {
-        for (int i = tid; i < 64 * kPanel; i += 256) {
-            const int rr = i % 64, cc = i / 64;
-            const int64_t r = t0 + rr;
-            const bool in = r < re;
-            V1s[rr][cc] = in ? A[r + (J0 + cc) * lda] : 0.0;
-            V2s[rr][cc] = (in && cc < nb2) ? vmask(A, lda, r, J0 + kPanel, cc) : 0.0;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int rr = 0; rr < 64; ++rr) {
-            const double v1 = V1s[rr][a];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = fma(v1, V2s[rr][4 * bq + i], acc[i]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) part[(int64_t)blockIdx.x * kPanel * kPanel + a + (4 * bq + i) * kPanel] = acc[i];
-}
-
-// part[0][e] = sum over the nparts partials of entry e (a warp per entry, fixed order).
-__global__ void __launch_bounds__(256) k_gsum(double* part, int nparts) {
-    const int lane = threadIdx.x & 31;
-    const int e = (blockIdx.x * 256 + threadIdx.x) >> 5;
-    if (e >= kPanel * kPanel) return;
-    double t = 0.0;
-    for (int k = lane; k < nparts; k += 32) t += part[(int64_t)k * kPanel * kPanel + e];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) part[e] = t;
-}
-
-// Tb (kOB x kOB, column-major) = [[T1, -T1 G12 T2], [0, T2]] with G12 the sum of the partials
-// (fixed order); T1, T2 are the panels' 32 x 32 T, nb2 the second panel's width.
-__global__ void __launch_bounds__(256) k_tmerge(const double* T1, const double* T2, const double* part, int nparts,
-                                                int nb2, double* Tb) {
-    __shared__ double G[kPanel * kPanel], X[kPanel * kPanel], t1[kPanel * kPanel], t2[kPanel * kPanel];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kPanel * kPanel; i += 256) {
-        double t = 0.0;
-        for (int k = 0; k < nparts; ++k) t += part[(int64_t)k * kPanel * kPanel + i];
-        G[i] = t;
-        t1[i] = T1[i];
-        t2[i] = T2[i];
-    }
-    __syncthreads();
-    for (int i = tid; i < kPanel * kPanel; i += 256) {   // X = G12 T2
-        const int a = i % kPanel, b = i / kPanel;
-        double t = 0.0;
-        for (int k = 0; k < nb2; ++k) t += G[a + k * kPanel] * t2[k + b * kPanel];
-        X[i] = t;
-    }
-    __syncthreads();
-    for (int i = tid; i < kOB * kOB; i += 256) {
-        const int a = i % kOB, b = i / kOB;
-        double v = 0.0;
-        if (a < kPanel && b < kPanel) {
-            v = t1[a + b * kPanel];
-        } else if (a >= kPanel && b >= kPanel) {
-            v = t2[(a - kPanel) + (b - kPanel) * kPanel];
-        } else if (a < kPanel && b >= kPanel) {   // -(T1 X)(a, b - 32)
-            double t = 0.0;
-            for (int k = 0; k < kPanel; ++k) t += t1[a + k * kPanel] * X[k + (b - kPanel) * kPanel];
-            v = -t;
-        }
-        Tb[i] = v;
-    }
-}
-
-// Tb = T1 zero-padded to kOB x kOB (outer block with one panel).
-__global__ void k_tpad(const double* T1, double* Tb) {
-    for (int i = threadIdx.x; i < kOB * kOB; i += blockDim.x) {
-        const int a = i % kOB, b = i / kOB;
-        Tb[i] = (a < kPanel && b < kPanel) ? T1[a + b * kPanel] : 0.0;
-    }
-}
-
-// ------------------------------------------------------------------ W = V^T C  (split over row chunks)
-
-constexpr int kVtcCols = 32;
-constexpr int kVtcPad = 8;                     // bf16 elements of padding per k-row
-constexpr int kVtcLdk = kVtcStep + kVtcPad;    // 40
-
-struct VtcSmem {
-    unsigned short As[2][kDig][kOB][kVtcLdk];     // V^T digits, two pipeline stages: [p][a][k]
-    long long Craw[2][kVtcCols][kVtcStep];        // raw fixed-point C rows, two stages: [c][k]
-    unsigned short Bs[kDig][kVtcCols][kVtcLdk];   // C digits of the current step: [q][c][k]
-};
-
-// Wp[chunk](a, c) for c in the column tile: sum over the chunk's rows of V(r, a) C(r, c).
-// Tile: all kOB rows of W x 32 columns, so each C digit feeds 64 outputs. Two-stage cp.async
-// pipeline: the V^T digits and raw C rows of step k + 1 are in flight while step k is cut
-// into digits and multiplied.
-__global__ void __launch_bounds__(kEmuThreads, 2)
-k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, int nbo, int64_t kc,
-          const unsigned short* VTd, int64_t ldv, const int* ecol, const int* E, double* Wp, int64_t nprime) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    VtcSmem& sm = *reinterpret_cast<VtcSmem*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const int64_t jc = J0 + nbo;
-    const int64_t c0 = (int64_t)blockIdx.x * kVtcCols;
+template <bool SMEM>
+__global__ void __launch_bounds__(kObThreads, 1)
+k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk, const int* E, double* tau,
+          double* Tb, unsigned short* Vd, unsigned short* VTd, int64_t ldvp, int* frow, int* ecol, double* part,
+          GridBarrier* bar, long long spin, int* err) {
+    extern __shared__ __align__(16) double ob_dyn[];
+    __shared__ double red[kRedSlots];
+    __shared__ double wk[kOB];
+    __shared__ double taus[kOB];
+    __shared__ double cmax[kOB];
+    __shared__ double gT[kOB * kOB];   // Gram columns (strict upper part), turned into T by CTA 0
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t L = s - J0;
-    const int64_t lb = (int64_t)blockIdx.y * kc;               // local row range [lb, le)
-    const int64_t le = lb + kc < L ? lb + kc : L;
-    const int mi = warp & 3, nt = warp >> 2;                   // warp: a in mi*16.., cols nt*16..
-    // Per output, the level sums are packed into two int64 fixed-point words:
-    // hi = sum_{l<3} T_l 2^(8 (2 - l)), lo = sum_{l>=3} T_l 2^(8 (5 - l)); per K-step each T_l < 2^22,
-    // so both stay below 2^50 over 1600 steps.
-    long long hi[2][4], lo[2][4];
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int h = 0; h < 4; ++h) { hi[j][h] = 0; lo[j][h] = 0; }
+    const int64_t r0 = J0 + (int64_t)g * chunk;
+    const int64_t r1 = r0 + chunk < s ? r0 + chunk : s;
+    const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
+    long long* Af = reinterpret_cast<long long*>(A);
+    double* W;
+    int64_t ldw;
+    if (SMEM) {
+        W = ob_dyn;
+        ldw = chunk;
+    } else {
+        W = A + r0 + J0 * lda;
+        ldw = lda;
+    }
+    // fixed point -> binary64: this CTA's rows of the block, and (grid-stride) rows 0 .. J0 - 1
+    for (int c = 0; c < nbo; ++c) {
+        const int e = E[J0 + c];
+        const int64_t base = (J0 + c) * lda;
+        for (int r = tid; r < nloc; r += kObThreads) {
+            const long long v = Af[base + r0 + r];
+            W[c * ldw + r] = e > -1000 ? ldexp((double)v, e - kFixBits) : 0.0;
+        }
+    }
+    for (int64_t idx = (int64_t)g * kObThreads + tid; idx < J0 * nbo; idx += (int64_t)G * kObThreads) {
+        const int64_t c = J0 + idx / J0, r = idx % J0;
+        const int e = E[c];
+        A[r + c * lda] = e > -1000 ? ldexp((double)Af[r + c * lda], e - kFixBits) : 0.0;
+    }
+    for (int i = tid; i < kOB * kOB; i += kObThreads) gT[i] = 0.0;
+    __syncthreads();
 
-    auto issue = [&](int stage, int64_t k0) {
-        // V^T digits: per (p, a) 32 contiguous bf16 = 4 chunks of 16 B
-        for (int idx = tid; idx < kDig * kOB * 4; idx += kEmuThreads) {
-            const int ch = idx & 3, a = (idx >> 2) % kOB, p = (idx >> 2) / kOB;
-            const int64_t lr = k0 + ch * 8;
-            const bool ok = lr < ldv;
-            const unsigned short* src = VTd + ((int64_t)p * kOB + a) * ldv + (ok ? lr : 0);
-            cp_async16(&sm.As[stage][p][a][ch * 8], src, ok ? 16 : 0);
+    auto own = [&](int64_t row) { return row >= r0 && row < r1; };
+    // Per step the CTAs exchange (a) summed partials, 128 slots per CTA: sigma (slot 0), d_k (slot k,
+    // k = 1..63), the Gram entries v_a^T v_c (slot 64 + a, a = 0..62) and the column maximum (slot
+    // 127), stored CTA-major so that a reduction reads each CTA's slots contiguously; (b) the owner
+    // CTA's diagonal-row values alpha and top_k (own[0], own[k]), which need no reduction. Both come in
+    // two buffers that alternate by step, so a CTA that runs ahead never overwrites values another
+    // CTA is still reading.
+    constexpr int kSlots = 128, kSlotMax = 127, kSlotGram = 64;
+    double* const own_base = part + 2 * (int64_t)G * kSlots;
+    auto sums = [&](int step) { return part + (int64_t)(step & 1) * G * kSlots + (int64_t)g * kSlots; };
+    auto owns = [&](int step) { return own_base + (step & 1) * (kOB + 1); };
+    // two interleaved accumulators per lane, combined in a fixed order
+    auto dot_tail = [&](const double* xs, const double* ys, int rs) {
+        double a0 = 0.0, a1 = 0.0;
+        int r = rs + lane;
+        for (; r + 32 < nloc; r += 64) {
+            a0 += xs[r] * ys[r];
+            a1 += xs[r + 32] * ys[r + 32];
         }
-        // raw C: per column 32 rows = 16 chunks of two int64
-        for (int idx = tid; idx < kVtcCols * (kVtcStep / 2); idx += kEmuThreads) {
-            const int ch = idx % (kVtcStep / 2), c = idx / (kVtcStep / 2);
-            const int64_t lr = k0 + 2 * ch, gc = jc + c0 + c;
-            const int rows = (gc < n) ? (int)(le - lr < 0 ? 0 : (le - lr > 2 ? 2 : le - lr)) : 0;
-            const long long* src = Cfix + (rows > 0 ? (J0 + lr) + gc * lda : 0);
-            cp_async16(&sm.Craw[stage][c][2 * ch], src, rows * 8);
+        if (r < nloc) a0 += xs[r] * ys[r];
+        double acc = a0 + a1;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        return acc;
+    };
+    // partial sums that column c (global row jj = J0 + c) needs, written for step c
+    auto column_sums = [&](int c) {
+        const int64_t jj = J0 + c;
+        const int rs = (int)(jj + 1 - r0 > 0 ? (jj + 1 - r0 < nloc ? jj + 1 - r0 : nloc) : 0);
+        double* ps = sums(c);
+        double* po = owns(c);
+        const int ntask = nbo - c;   // task 0: sigma; task t >= 1: d_{c+t}
+        for (int t = warp; t < ntask; t += kObWarps) {
+            const double acc = dot_tail(W + c * ldw, W + (c + t) * ldw, rs);
+            if (lane == 0) {
+                ps[t == 0 ? 0 : c + t] = acc;
+                if (own(jj)) po[t == 0 ? 0 : c + t] = W[(c + t) * ldw + (jj - r0)];
+            }
         }
-        cp_async_commit();
+    };
+    // Gram column of reflector c (a < c) and its column maximum, written for step c + 1
+    auto gram_sums = [&](int c) {
+        const int64_t jj = J0 + c;
+        const int rs = (int)(jj + 1 - r0 > 0 ? (jj + 1 - r0 < nloc ? jj + 1 - r0 : nloc) : 0);
+        double* ps = sums(c + 1);
+        for (int t = warp; t <= c; t += kObWarps) {
+            const double* vc = W + c * ldw;
+            if (t < c) {
+                double acc = dot_tail(W + t * ldw, vc, rs);
+                if (lane == 0) {
+                    if (own(jj)) acc += W[t * ldw + (jj - r0)];   // v_c = 1 on its diagonal row
+                    ps[kSlotGram + t] = acc;
+                }
+            } else {
+                double mx = 1.0;   // the unit diagonal entry
+                for (int r = rs + lane; r < nloc; r += 32) mx = fmax(mx, fabs(vc[r]));
+                for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (lane == 0) ps[kSlotMax] = mx;
+            }
+        }
+    };
+    // Reduction at the barrier of step c: thread (phase h, slot s) sums the slot over CTAs h, h + 4,
+    // ... (independent loads, coalesced across the slots), then the four phases are added in a fixed
+    // order; all CTAs obtain the same bits. Live slots: sigma and d_k (c < k < nbo) for column c,
+    // Gram a < c - 1 and the maximum of reflector c - 1.
+    __shared__ double red4[4][kSlots];
+    auto reduce_step = [&](int c) {
+        const int sl = tid & (kSlots - 1), h = tid >> 7;
+        const bool live = (sl == 0 && c < nbo) || (sl >= 1 && sl < kOB && sl > c && sl < nbo) ||
+                          (sl >= kSlotGram && sl < kSlotMax && sl - kSlotGram < c - 1) || (sl == kSlotMax && c >= 1);
+        double acc = 0.0;
+        if (live) {
+            const double* src = part + (int64_t)(c & 1) * G * kSlots + sl;
+            if (sl == kSlotMax)
+                for (int q = h; q < G; q += 4) acc = fmax(acc, __ldcg(src + (int64_t)q * kSlots));
+            else
+                for (int q = h; q < G; q += 4) acc += __ldcg(src + (int64_t)q * kSlots);
+        }
+        red4[h][sl] = acc;
+        __syncthreads();
+        if (tid < kSlots) {
+            const double v = tid == kSlotMax ? fmax(fmax(red4[0][tid], red4[1][tid]), fmax(red4[2][tid], red4[3][tid]))
+                                             : ((red4[0][tid] + red4[1][tid]) + red4[2][tid]) + red4[3][tid];
+            if (tid == 0) red[kRedSig] = v;
+            else if (tid < kOB) red[kRedD + tid] = v;
+            else if (tid < kSlotMax) red[kRedGram + tid - kSlotGram] = v;
+            else red[kRedMax] = v;
+        } else if (tid < kSlots + kOB && c < nbo) {
+            const int k = tid - kSlots;   // owner values of column c
+            const double v = __ldcg(owns(c) + k);
+            if (k == 0) red[kRedAlpha] = v;
+            else if (k > c && k < nbo) red[kRedTop + k] = v;
+        }
     };
 
-    int stage = 0;
-    issue(0, lb);
-    for (int64_t k0 = lb; k0 < le; k0 += kVtcStep) {
-        if (k0 + kVtcStep < le) issue(stage ^ 1, k0 + kVtcStep);
-        else cp_async_commit();                                // keep the group count uniform
-        cp_async_wait<1>();
+    column_sums(0);
+    for (int c = 0; c <= nbo; ++c) {
+        if (!grid_sync(bar, G, spin, err)) return;
+        reduce_step(c);
         __syncthreads();
-        // cut this step's C entries into digits: a warp takes the 32 rows of one column at a time, so
-        // its int64 reads from shared memory are consecutive words (no bank conflicts)
-#pragma unroll
-        for (int e = 0; e < (kVtcCols * kVtcStep) / kEmuThreads; ++e) {
-            const int idx = e * kEmuThreads + tid;
-            const int c = idx / kVtcStep, k = idx % kVtcStep;
-            int d[kDig];
-            digits_fix(sm.Craw[stage][c][k], d);
-#pragma unroll
-            for (int q = 0; q < kDig; ++q) sm.Bs[q][c][k] = bf16_of_int(d[q]);
+        if (c >= 1) {   // Gram column and maximum of reflector c - 1
+            for (int a = tid; a < c - 1; a += kObThreads) gT[a + (c - 1) * kOB] = red[kRedGram + a];
+            if (tid == 0) cmax[c - 1] = red[kRedMax];
         }
-        __syncthreads();
-#pragma unroll
-        for (int l = 0; l <= kLev; ++l) {
-            float acc[2][4] = {{kMagic, kMagic, kMagic, kMagic}, {kMagic, kMagic, kMagic, kMagic}};
-#pragma unroll
-            for (int p = 0; p <= l; ++p) {
-                const int q = l - p;
-#pragma unroll
-                for (int ks = 0; ks < kVtcStep; ks += 16) {
-                    uint32_t af[4], bq[4];
-                    ldsm_x4(af, &sm.As[stage][p][mi * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
-                    ldsm_x4(bq, &sm.Bs[q][nt * 16 + (lane & 7) + ((lane >> 4) & 1) * 8][ks + ((lane >> 3) & 1) * 8]);
-                    const uint32_t b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
-                    hmma(acc[0], af, b0);
-                    hmma(acc[1], af, b1);
-                }
+        if (c == nbo) break;
+        const int64_t jj = J0 + c;
+        // reflector of column c (every thread forms the same scalars)
+        const double sigma = red[kRedSig], alpha = red[kRedAlpha];
+        double tau_c = 0.0, scal = 1.0, beta = alpha;
+        const bool live = sigma != 0.0;
+        if (live) {
+            const double nrm = sqrt(alpha * alpha + sigma);
+            beta = alpha >= 0.0 ? -nrm : nrm;
+            tau_c = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+        }
+        if (tid < kOB) wk[tid] = (tid > c && tid < nbo) ? tau_c * (red[kRedTop + tid] + scal * red[kRedD + tid]) : 0.0;
+        if (tid == 0) {
+            taus[c] = tau_c;
+            if (g == 0) tau[jj] = tau_c;
+        }
+        const int rj = (int)(jj - r0);   // local index of the diagonal row (may be outside [0, nloc))
+        if (live) {
+            for (int r = tid; r < nloc; r += kObThreads) {
+                if (r > rj) W[c * ldw + r] *= scal;
+                else if (r == rj) W[c * ldw + r] = beta;
             }
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const long long v = (long long)magic_to_int(acc[j][h]);
-                    if (l < 3) hi[j][h] += v << (8 * (2 - l));
-                    else lo[j][h] += v << (8 * (5 - l));
-                }
         }
         __syncthreads();
-        stage ^= 1;
+        // A(j:s, k) -= w_k v for the later block columns (rows of this CTA)
+        if (live) {
+            const int rs = rj > 0 ? (rj < nloc ? rj : nloc) : 0;
+            for (int k = c + 1 + warp; k < nbo; k += kObWarps) {
+                const double w = wk[k];
+                double* col = W + k * ldw;
+                const double* v = W + c * ldw;
+                for (int r = rs + lane; r < nloc; r += 32) col[r] -= w * (r == rj ? 1.0 : v[r]);
+            }
+        }
+        __syncthreads();
+        if (c + 1 < nbo) column_sums(c + 1);
+        gram_sums(c);
+        __syncthreads();
     }
-    cp_async_wait<0>();
-    // W(a, c) = 2^(e_a + E_c - 14) sum_l 2^(-8 l) T_l   (C entries carry scale 2^(E_c - 47))
-    double* out = Wp + (int64_t)blockIdx.y * kOB * nprime;
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int a = mi * 16 + g + (h >> 1) * 8;
-            const int64_t col = c0 + nt * 16 + j * 8 + 2 * t + (h & 1);
-            if (col < nprime && a < nbo) {
-                const int sc = ecol[a] + E[jc + col] - 14;
-                const double v = ldexp((double)hi[j][h], -16) + ldexp((double)lo[j][h], -40);
-                out[(int64_t)a * nprime + col] = ldexp(v, sc);
+    // T of the block (CTA 0)
+    if (g == 0) {
+        for (int i = 0; i < nbo; ++i) {
+            double v = 0.0;
+            if (tid < i) {
+                double acc = 0.0;
+                for (int b = tid; b < i; ++b) acc += gT[tid + b * kOB] * gT[b + i * kOB];
+                v = -taus[i] * acc;
             }
+            __syncthreads();
+            if (tid < i) gT[tid + i * kOB] = v;
+            if (tid == i) gT[i + i * kOB] = taus[i];
+            __syncthreads();
         }
+        for (int i = tid; i < kOB * kOB; i += kObThreads) {
+            const int a = i % kOB, b = i / kOB;
+            Tb[i] = (a <= b && b < nbo) ? gT[i] : 0.0;
+        }
+    }
+    // column exponents of V (for V^T C) and the digits of this CTA's rows
+    __shared__ int ecol_s[kOB];
+    if (tid < kOB) {
+        ecol_s[tid] = tid < nbo ? exp_of(cmax[tid]) : 0;
+        if (g == 0) ecol[tid] = ecol_s[tid];
+    }
+    __syncthreads();
+    for (int r = tid; r < nloc; r += kObThreads) {
+        const int64_t grow = r0 + r, lr = grow - J0;
+        double mx = 0.0;
+        for (int a = 0; a < nbo; ++a) {
+            const int64_t d = J0 + a;
+            const double v = grow < d ? 0.0 : (grow == d ? 1.0 : W[a * ldw + r]);
+            mx = fmax(mx, fabs(v));
+        }
+        const int f = exp_of(mx);
+        frow[lr] = f;
+        for (int a0 = 0; a0 < kOB; a0 += 8) {
+            uint32_t pk[kDig][4];
+#pragma unroll
+            for (int jq = 0; jq < 8; ++jq) {
+                const int a = a0 + jq;
+                const int64_t d = J0 + a;
+                const double v = a < nbo ? (grow < d ? 0.0 : (grow == d ? 1.0 : W[a * ldw + r])) : 0.0;
+                int dg[kDig], dt[kDig];
+                digits_f64(v, f, dg);
+                digits_f64(v, ecol_s[a], dt);
+#pragma unroll
+                for (int p = 0; p < kDig; ++p) {
+                    const uint32_t h = bf16_of_int(dg[p]);
+                    if (jq & 1) pk[p][jq >> 1] |= h << 16;
+                    else pk[p][jq >> 1] = h;
+                    VTd[vtd_index(p, a, lr)] = bf16_of_int(dt[p]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < kDig; ++p)
+                reinterpret_cast<uint4*>(Vd)[vd_chunk(p, lr, a0 >> 3)] = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+        }
+    }
+    // padding rows L .. ldvp - 1 of the digit planes: zero digits
+    for (int64_t lr = L + (int64_t)g * kObThreads + tid; lr < ldvp; lr += (int64_t)G * kObThreads) {
+        frow[lr] = 0;
+        const uint32_t z = (uint32_t)bf16_of_int(0) * 0x10001u;
+        for (int a0 = 0; a0 < kOB; a0 += 8)
+            for (int p = 0; p < kDig; ++p) reinterpret_cast<uint4*>(Vd)[vd_chunk(p, lr, a0 >> 3)] = make_uint4(z, z, z, z);
+        for (int p = 0; p < kDig; ++p)
+            for (int a = 0; a < kOB; ++a) VTd[vtd_index(p, a, lr)] = (unsigned short)(z & 0xFFFFu);
+    }
+    if (SMEM) {   // the factored rows back to the matrix, in binary64
+        for (int c = 0; c < nbo; ++c)
+            for (int r = tid; r < nloc; r += kObThreads) A[(r0 + r) + (J0 + c) * lda] = W[c * ldw + r];
+    }
 }
 
 // ------------------------------------------------------------------ C += V Wn  (exact integer update, tcgen05)
@@ -551,8 +514,10 @@ k_emu_vtc(const long long* Cfix, int64_t lda, int64_t s, int64_t n, int64_t J0, 
 //                        for C;
 //   warp 1 (one thread)  tcgen05.mma: per level l the products of digit pairs p + q = l
 //                        accumulate in their own FP32 TMEM block (exact: every level sum is an
-//                        integer below 6 x 64 x 2^14 < 2^23); two accumulator sets of 6 x 32
-//                        columns, so the MMAs of tile i + 1 run while tile i is written back;
+//                        integer below 6 x 64 x 2^14 < 2^23); one MMA per V plane p and K step
+//                        covers the levels p .. 5 (Wn planes stacked along N); two accumulator
+//                        sets of 6 x 32 columns, so the MMAs of tile i + 1 run while tile i is
+//                        written back;
 //   warps 2..9           epilogue: TMEM -> registers, levels combined in int64, scaled onto the
 //                        column's fixed-point grid and added to the staged C entry; one thread
 //                        per row and 16 columns, so each column store of a warp is 256
@@ -574,7 +539,7 @@ struct TcUpdSmem {
     unsigned char A[kDig][kTcPlaneA];
     unsigned char B[2][kDig][kTcPlaneB];
     long long C[2][kTcN][kTcM];
-    uint64_t full_a, full_b[2], full_c[2], done[2], freed[2], drain;
+    uint64_t full_a, full_b[2], full_c[2], done[2], tfree[2], freed[2], drain;
     uint32_t tmem;
     int abort;
 };
@@ -590,7 +555,7 @@ __device__ __forceinline__ void tensor_g2s_2d(void* dst, const CUtensorMap* map,
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo,
-                const unsigned short* Vd, const int* frow, const unsigned short* Wd, const int* gcol, const int* E,
+                const unsigned short* Vd, const int* frow, const unsigned short* Wd, const int* gsh,
                 int64_t nprime, int cpt, long long spin, int* err) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     TcUpdSmem& sm = *reinterpret_cast<TcUpdSmem*>(tc_smem_raw);
@@ -612,6 +577,7 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
             tc::mbar_init(&sm.full_b[b], 1);
             tc::mbar_init(&sm.full_c[b], 1);
             tc::mbar_init(&sm.done[b], 1);
+            tc::mbar_init(&sm.tfree[b], 32 * kTcEpiWarps);
             tc::mbar_init(&sm.freed[b], 32 * kTcEpiWarps);
         }
         tc::mbar_init(&sm.drain, 1);
@@ -626,13 +592,16 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
 
     if (warp == 0) {
         if (lane == 0) {
-            int armed0 = 0, armed1 = 0;   // uses of each stage whose copies were issued
+            // uses of each stage whose B (Wn digits) and C copies were issued
+            int armedB0 = 0, armedB1 = 0, armedC0 = 0, armedC1 = 0;
             tc::mbar_arrive_expect_tx(&sm.full_a, kDig * kTcPlaneA);
             tc::bulk_g2s(sm.A[0], reinterpret_cast<const unsigned char*>(Vd) + rt * (kDig * kTcPlaneA),
                          kDig * kTcPlaneA, &sm.full_a);
             for (int i = 0; i < ntile; ++i) {
                 const int b = i & 1, u = i >> 1;
-                if (u > 0 && !tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
+                // stage b's Wn digits are free once tile i - 2's accumulators were read (its MMAs are
+                // done); its C block once tile i - 2's write-back has read it
+                if (u > 0 && !tc::mbar_wait(&sm.tfree[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
                     *abort = 1;
                     set_error(err, CSLS_ERR_TIMEOUT);
                     break;
@@ -641,56 +610,58 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                 tc::mbar_arrive_expect_tx(&sm.full_b[b], kDig * kTcPlaneB);
                 tc::bulk_g2s(sm.B[b][0], reinterpret_cast<const unsigned char*>(Wd) + ct * (kDig * kTcPlaneB),
                              kDig * kTcPlaneB, &sm.full_b[b]);
+                if (b) armedB1 = u + 1;
+                else armedB0 = u + 1;
+                if (u > 0 && !tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
+                    *abort = 1;
+                    set_error(err, CSLS_ERR_TIMEOUT);
+                    break;
+                }
                 tc::mbar_arrive_expect_tx(&sm.full_c[b], kTcN * kTcM * 8);
                 tensor_g2s_2d(sm.C[b][0], &cmap, (int)(J0 + rb), (int)(jc + ct * kTcN), &sm.full_c[b]);
-                if (b) armed1 = u + 1;
-                else armed0 = u + 1;
+                if (b) armedC1 = u + 1;
+                else armedC0 = u + 1;
             }
             // copies in flight land before the CTA can leave. Issued copies always complete, so
             // these waits are bounded by wall time only (not by the caller's spin count, which
             // may be tiny): a CTA never exits with a copy still writing its shared memory.
             tc::mbar_wait(&sm.full_a, 0, kTeardownSpin, kTcWaitNs, nullptr);
-            if (armed0) {
-                tc::mbar_wait(&sm.full_b[0], (armed0 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
-                tc::mbar_wait(&sm.full_c[0], (armed0 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
-            }
-            if (armed1) {
-                tc::mbar_wait(&sm.full_b[1], (armed1 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
-                tc::mbar_wait(&sm.full_c[1], (armed1 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
-            }
+            if (armedB0) tc::mbar_wait(&sm.full_b[0], (armedB0 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
+            if (armedC0) tc::mbar_wait(&sm.full_c[0], (armedC0 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
+            if (armedB1) tc::mbar_wait(&sm.full_b[1], (armedB1 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
+            if (armedC1) tc::mbar_wait(&sm.full_c[1], (armedC1 - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
             bool issued = false;
             if (tc::mbar_wait(&sm.full_a, 0, spin, kTcWaitNs, abort)) {
-                const uint32_t idesc = tc::idesc_bf16_f32(kTcM, kTcN);
                 const uint64_t adesc = tc::smem_desc(tc::smem_addr(sm.A[0]), kTcM * 16, 128);
                 for (int i = 0; i < ntile; ++i) {
                     const int b = i & 1, u = i >> 1;
                     // the accumulator set of this stage was drained by the epilogue of tile i - 2
-                    if ((u > 0 && !tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) ||
+                    if ((u > 0 && !tc::mbar_wait(&sm.tfree[b], (u - 1) & 1, spin, kTcWaitNs, abort)) ||
                         !tc::mbar_wait(&sm.full_b[b], u & 1, spin, kTcWaitNs, abort)) {
                         *abort = 1;
                         set_error(err, CSLS_ERR_TIMEOUT);
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint64_t bdesc = tc::smem_desc(tc::smem_addr(sm.B[b][0]), kTcN * 16, 128);
+                    const uint64_t bdesc = tc::smem_desc(tc::smem_addr(sm.B[b][0]), kTcNStack * 16, 128);
                     const uint32_t d0 = tmem + (uint32_t)(b * kTcBufCols);
-                    // 84 MMAs, fully unrolled: each descriptor is the stage's base plus a constant
-                    // (the start address sits in the low bits, in 16-byte units); a K step of 16 is
-                    // two core-matrix columns
+                    // 24 MMAs, fully unrolled: for V plane p one MMA per K step of 16 against the
+                    // stacked Wn planes 0 .. 5 - p (N = 32 (6 - p)), accumulating levels p .. 5 in
+                    // their adjacent TMEM blocks. The first MMA (p = 0, N = 192) starts every level
+                    // block from zero. Each descriptor is the stage's base plus a constant (the start
+                    // address sits in the low bits, in 16-byte units); a K step is two core matrices.
 #pragma unroll
-                    for (int l = 0; l <= kLev; ++l)
+                    for (int p = 0; p <= kLev; ++p)
 #pragma unroll
-                        for (int p = 0; p <= l; ++p)
-#pragma unroll
-                            for (int k = 0; k < kOB / 16; ++k)
-                                tc::mma_bf16(d0 + l * kTcN,
-                                             adesc + (uint64_t)((p * kTcPlaneA + k * 2 * (kTcM * 16)) >> 4),
-                                             bdesc + (uint64_t)(((l - p) * kTcPlaneB + k * 2 * (kTcN * 16)) >> 4),
-                                             idesc, (p | k) != 0);
+                        for (int k = 0; k < kOB / 16; ++k)
+                            tc::mma_bf16(d0 + p * kTcN,
+                                         adesc + (uint64_t)((p * kTcPlaneA + k * 2 * (kTcM * 16)) >> 4),
+                                         bdesc + (uint64_t)((k * 2 * (kTcNStack * 16)) >> 4),
+                                         tc::idesc_bf16_f32(kTcM, kTcN * (kDig - p)), (p | k) != 0);
                     tc::mma_commit(&sm.done[b]);
                     issued = true;
                 }
@@ -728,20 +699,26 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
             for (int l = 0; l < kTcLevels; ++l) tc::tmem_ld16(ta + l * kTcN, v[l]);
             tc::tmem_ld_wait();
             tc::fence_before_sync();
+            tc::mbar_arrive(&sm.tfree[b]);   // the accumulator set may take tile i + 2's MMAs now
             const int64_t cbase = (ct0 + i) * kTcN + half * 16;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int64_t col = cbase + j;
                 if (rok && col < nprime) {
-                    long long acc = 0;
-#pragma unroll
-                    for (int l = 0; l < kTcLevels; ++l)
-                        acc = acc * 256 + (long long)__float2int_rn(__uint_as_float(v[l][j]));
-                    // Cfix += acc * 2^(f_r + g_c - 14 - 8 kLev + 62 - E_c), rounded to the fixed-point grid
-                    const int sh = fr + gcol[col] - 14 - 8 * kLev + kFixBits - E[jc + col];
+                    // acc = sum_l T_l 256^(5 - l): T_0 256 + T_1 fits 32 bits (|T_0| <= 64 x 2^14), the
+                    // rest is three 32 x 32 -> 64-bit multiply-adds
+                    const int t0 = __float2int_rn(__uint_as_float(v[0][j]));
+                    const int t1 = __float2int_rn(__uint_as_float(v[1][j]));
+                    const int t2 = __float2int_rn(__uint_as_float(v[2][j]));
+                    const int t3 = __float2int_rn(__uint_as_float(v[3][j]));
+                    const int t4 = __float2int_rn(__uint_as_float(v[4][j]));
+                    const int t5 = __float2int_rn(__uint_as_float(v[5][j]));
+                    long long acc = (long long)t2 * (1LL << 24) + ((long long)t3 * 65536 + ((long long)t4 * 256 + t5));
+                    acc += (long long)(t0 * 256 + t1) << 32;
+                    // Cfix += acc * 2^(f_r + gsh_c), rounded to the fixed-point grid
+                    const int sh = fr + gsh[col];
                     long long dlt;
-                    if (acc == 0) dlt = 0;
-                    else if (sh >= 0) dlt = sh < 63 ? acc << sh : 0;
+                    if (sh >= 0) dlt = sh < 63 ? acc << sh : 0;
                     else dlt = -sh < 63 ? (acc + (1LL << (-sh - 1))) >> (-sh) : 0;
                     Cfix[(J0 + lr) + (jc + col) * lda] = sm.C[b][half * 16 + j][r] + dlt;
                 }
@@ -753,6 +730,268 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
     if (warp == 1) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, kTcTmemCols);
+    }
+}
+
+// ------------------------------------------------------------------ W = V^T C on tcgen05 (split over row chunks)
+//
+// One CTA per (128-column tile of C, chunk of rows). The product is D = C^T V (128 C columns on
+// the TMEM lanes x 64 V columns), cut into digit planes: C digits (A operand, plane q) times V
+// digits (B operand). The six V planes are stacked along N (row p x 64 + a of a 384-row operand),
+// so one MMA multiplies C plane q by V planes p0 .. p0 + w - 1 and accumulates levels q + p0 ..
+// q + p0 + w - 1, whose 64-column TMEM blocks are adjacent (levels 0..5 occupy columns 0..383).
+// Levels p + q <= 5 are kept: per K step of 16 rows 8 MMAs (N <= 256) cover the 21 digit pairs.
+// Level sums are exact in FP32 while below 2^24; a window of 128 rows keeps them below
+// 6 x 128 x 2^14 = 1.5 x 2^23, after which the drain warps fold the window into one int64 per
+// output, sum_l T_l 2^(8 (5 - l)). That int64 stays below 2^54 sqrt(rows) (Cauchy-Schwarz with
+// |N_v| < 2^47 and sum_r N_c(r)^2 < 2^94 from the column-norm scale), so chunks of up to 2^14 rows
+// cannot overflow it.
+// Roles (448 threads):
+//   warp 0 (one thread)  copies: per K-block of 32 rows the raw int64 C rows (two 16-row x 128-
+//                        column tensor boxes, 128-byte swizzle) and the block's V digits (one 24 KB
+//                        bulk copy; the panel kernel writes them in this K-major core-matrix order);
+//   warp 1 (one thread)  the MMAs, two stages of operands;
+//   warps 2..5           cut the raw C rows into six bf16 digit planes in shared memory (one C
+//                        column per thread, read through the swizzle without bank conflicts);
+//   warps 6..13          drain the TMEM level sums every window into int64 registers (one C
+//                        column per thread and 32 V columns) and write the chunk's partial W.
+// Every wait is bounded (spin polls and wall time); a role that gives up sets the abort flag and
+// the error word; copies and MMAs in flight are still awaited (wall time only) before the CTA frees
+// its tensor memory and exits.
+constexpr int kVcM = 128;                           // C columns per tile (TMEM lanes)
+constexpr int kVcKB = 32;                           // rows per K-block (pipeline stage)
+constexpr int kVcWin = 4;                           // K-blocks per exact accumulation window (128 rows)
+constexpr int kVcNStack = kDig * kOB;               // 384 rows of the stacked V-digit operand
+constexpr int kVcPlaneA = kVcM * kVcKB * 2;         // 8 KB: one C-digit plane of a K-block
+constexpr int kVcBBytes = kVcNStack * kVcKB * 2;    // 24 KB: the stacked V digits of a K-block
+constexpr int kVcRawBox = 16;                       // rows per raw-C tensor box (128 bytes)
+constexpr int kVcRawBytes = kVcM * kVcKB * 8;       // 32 KB of raw C per K-block
+constexpr int kVcCutWarps = 4, kVcDrainWarps = 8;
+constexpr int kVcThreads = 32 * (2 + kVcCutWarps + kVcDrainWarps);
+constexpr int kVcMaxChunk = 1 << 14;                // rows per chunk (int64 accumulator bound)
+
+struct VcSmem {
+    unsigned char raw[2][kVcRawBytes];              // 1024-byte aligned (swizzled tensor boxes)
+    unsigned char cd[2][kDig][kVcPlaneA];
+    unsigned char vd[2][kVcBBytes];
+    uint64_t full_raw[2], empty_raw[2], full_cd[2], full_vd[2], empty_op[2], acc_full, acc_empty, drain;
+    uint32_t tmem;
+    int abort;
+};
+
+__global__ void __maxnreg__(144)
+k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* VTd, int64_t J0, int nbo, int64_t L,
+             int64_t kc, const int* ecol, const int* E, double* Wp, int64_t nprime, long long spin, int* err) {
+    extern __shared__ __align__(1024) unsigned char vc_smem_raw[];
+    // the 128-byte swizzle of the raw-C boxes needs a 1024-byte aligned destination: the launch
+    // gives 1 KB of slack, the structure starts at the first 1024-byte boundary
+    const uint32_t base = tc::smem_addr(vc_smem_raw);
+    VcSmem& sm = *reinterpret_cast<VcSmem*>(vc_smem_raw + (((base + 1023u) & ~1023u) - base));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t jc = J0 + nbo;
+    const int64_t c0 = (int64_t)blockIdx.x * kVcM;
+    const int64_t lb = (int64_t)blockIdx.y * kc;
+    const int64_t le = lb + kc < L ? lb + kc : L;
+    const int nkb = (int)ceil_div_dev(le - lb, kVcKB);
+    const int nwin = (nkb + kVcWin - 1) / kVcWin;
+    volatile int* abort = &sm.abort;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&sm.full_raw[b], 1);
+            tc::mbar_init(&sm.empty_raw[b], 32 * kVcCutWarps);
+            tc::mbar_init(&sm.full_cd[b], 32 * kVcCutWarps);
+            tc::mbar_init(&sm.full_vd[b], 1);
+            tc::mbar_init(&sm.empty_op[b], 1);
+        }
+        tc::mbar_init(&sm.acc_full, 1);
+        tc::mbar_init(&sm.acc_empty, 32 * kVcDrainWarps);
+        tc::mbar_init(&sm.drain, 1);
+        sm.abort = 0;
+        tc::mbar_init_fence();
+    }
+    if (warp == 1) tc::tmem_alloc(&sm.tmem, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = sm.tmem;
+    auto fail = [&]() {
+        *abort = 1;
+        set_error(err, CSLS_ERR_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int armed0 = 0, armed1 = 0;   // uses of each stage whose copies were issued (negative: raw only)
+            for (int i = 0; i < nkb; ++i) {
+                const int st = i & 1, u = i >> 1;
+                if (u > 0 && !tc::mbar_wait(&sm.empty_raw[st], (u - 1) & 1, spin, kTcWaitNs, abort)) { fail(); break; }
+                const int64_t row = J0 + lb + (int64_t)i * kVcKB;
+                tc::mbar_arrive_expect_tx(&sm.full_raw[st], kVcRawBytes);
+                tensor_g2s_2d(sm.raw[st], &rawmap, (int)row, (int)(jc + c0), &sm.full_raw[st]);
+                tensor_g2s_2d(sm.raw[st] + kVcRawBytes / 2, &rawmap, (int)(row + kVcRawBox), (int)(jc + c0),
+                              &sm.full_raw[st]);
+                if (u > 0 && !tc::mbar_wait(&sm.empty_op[st], (u - 1) & 1, spin, kTcWaitNs, abort)) {
+                    if (st) armed1 = -(u + 1);   // raw copy issued, V copy not
+                    else armed0 = -(u + 1);
+                    fail();
+                    break;
+                }
+                tc::mbar_arrive_expect_tx(&sm.full_vd[st], kVcBBytes);
+                tc::bulk_g2s(sm.vd[st], reinterpret_cast<const unsigned char*>(VTd) + (lb + (int64_t)i * kVcKB) * (kVcNStack * 2),
+                             kVcBBytes, &sm.full_vd[st]);
+                if (st) armed1 = u + 1;
+                else armed0 = u + 1;
+            }
+            // copies in flight land before the CTA leaves (issued copies always complete)
+            for (int st = 0; st < 2; ++st) {
+                const int ar = st ? armed1 : armed0;
+                const int a = ar < 0 ? -ar : ar;
+                if (a == 0) continue;
+                tc::mbar_wait(&sm.full_raw[st], (a - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
+                if (ar > 0) tc::mbar_wait(&sm.full_vd[st], (a - 1) & 1, kTeardownSpin, kTcWaitNs, nullptr);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool issued = false;
+            const uint64_t bdA = tc::smem_desc(tc::smem_addr(sm.vd[0]), kVcNStack * 16, 128);
+            const uint64_t bdB = tc::smem_desc(tc::smem_addr(sm.vd[1]), kVcNStack * 16, 128);
+            const uint64_t adA = tc::smem_desc(tc::smem_addr(sm.cd[0][0]), kVcM * 16, 128);
+            const uint64_t adB = tc::smem_desc(tc::smem_addr(sm.cd[1][0]), kVcM * 16, 128);
+            for (int i = 0; i < nkb; ++i) {
+                const int st = i & 1, u = i >> 1, w = i / kVcWin;
+                const bool first = (i % kVcWin) == 0;
+                if ((first && w > 0 && !tc::mbar_wait(&sm.acc_empty, (w - 1) & 1, spin, kTcWaitNs, abort)) ||
+                    !tc::mbar_wait(&sm.full_cd[st], u & 1, spin, kTcWaitNs, abort) ||
+                    !tc::mbar_wait(&sm.full_vd[st], u & 1, spin, kTcWaitNs, abort)) {
+                    fail();
+                    break;
+                }
+                tc::fence_after_sync();
+#pragma unroll
+                for (int k = 0; k < kVcKB / 16; ++k) {
+                    const uint64_t ak = (st ? adB : adA) + (uint64_t)((k * 2 * (kVcM * 16)) >> 4);
+                    const uint64_t bk = (st ? bdB : bdA) + (uint64_t)((k * 2 * (kVcNStack * 16)) >> 4);
+                    const uint32_t z = (first && k == 0) ? 0u : 1u;
+                    // (q, p0, w): C plane q times V planes p0 .. p0 + w - 1 -> levels q + p0 ..
+#define VC_MMA(q, p0, wdt, acc)                                                                              \
+    tc::mma_bf16(tmem + (uint32_t)(kOB * ((q) + (p0))), ak + (uint64_t)(((q) * kVcPlaneA) >> 4),              \
+                 bk + (uint64_t)(((p0) * kOB * 16) >> 4), tc::idesc_bf16_f32(kVcM, kOB * (wdt)), (acc))
+                    VC_MMA(0, 0, 4, z);
+                    VC_MMA(0, 4, 2, z);
+                    VC_MMA(1, 0, 4, 1u);
+                    VC_MMA(1, 4, 1, 1u);
+                    VC_MMA(2, 0, 4, 1u);
+                    VC_MMA(3, 0, 3, 1u);
+                    VC_MMA(4, 0, 2, 1u);
+                    VC_MMA(5, 0, 1, 1u);
+#undef VC_MMA
+                }
+                tc::mma_commit(&sm.empty_op[st]);
+                if ((i % kVcWin) == kVcWin - 1 || i == nkb - 1) tc::mma_commit(&sm.acc_full);
+                issued = true;
+            }
+            if (issued) {   // every MMA has completed before the tensor memory is freed (wall-time bound only)
+                tc::mma_commit(&sm.drain);
+                tc::mbar_wait(&sm.drain, 0, kTeardownSpin, kTcWaitNs, nullptr);
+            }
+        }
+        __syncwarp();
+    } else if (warp < 2 + kVcCutWarps) {
+        // cutters: thread m owns C column m of the tile
+        const int m = threadIdx.x - 64;
+        for (int i = 0; i < nkb; ++i) {
+            const int st = i & 1, u = i >> 1;
+            const bool ok = tc::mbar_wait(&sm.full_raw[st], u & 1, spin, kTcWaitNs, abort) &&
+                            (u == 0 || tc::mbar_wait(&sm.empty_op[st], (u - 1) & 1, spin, kTcWaitNs, abort));
+            if (!ok) {
+                fail();
+                break;
+            }
+#pragma unroll 1
+            for (int kg = 0; kg < kVcKB / 8; ++kg) {
+                // rows 8 kg .. 8 kg + 7: box kg / 2, 16-byte chunks 4 (kg % 2) .. + 3 of row m (swizzled)
+                const unsigned char* box = sm.raw[st] + (kg >> 1) * (kVcRawBytes / 2) + m * 128;
+                long long cv[8];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int chunk = (4 * (kg & 1) + h) ^ (m & 7);
+                    const longlong2 t = *reinterpret_cast<const longlong2*>(box + chunk * 16);
+                    cv[2 * h] = t.x;
+                    cv[2 * h + 1] = t.y;
+                }
+                uint32_t pk[kDig][4];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    int d[kDig];
+                    digits_fix(cv[e], d);
+#pragma unroll
+                    for (int q = 0; q < kDig; ++q) {
+                        const uint32_t h = bf16_of_int(d[q]);
+                        if (e & 1) pk[q][e >> 1] |= h << 16;
+                        else pk[q][e >> 1] = h;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kDig; ++q)
+                    *reinterpret_cast<uint4*>(sm.cd[st][q] + (kg * kVcM + m) * 16) =
+                        make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
+            }
+            // generic-proxy shared-memory writes become visible to the tensor core (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc::mbar_arrive(&sm.full_cd[st]);
+            tc::mbar_arrive(&sm.empty_raw[st]);
+        }
+    } else {
+        // drain: TMEM lanes 32 (warp % 4) .. + 31, V columns 32 half .. + 31
+        const int quarter = warp & 3, half = (warp - 2 - kVcCutWarps) >> 2;
+        const int m = quarter * 32 + lane;
+        long long acc[32];
+#pragma unroll
+        for (int a = 0; a < 32; ++a) acc[a] = 0;
+        bool ok_all = true;
+        for (int w = 0; w < nwin; ++w) {
+            bool ok = tc::mbar_wait(&sm.acc_full, w & 1, spin, kTcWaitNs, abort);
+            ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld is warp-wide
+            if (!ok) {
+                fail();
+                ok_all = false;
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int l = 0; l <= kLev; ++l)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kOB * l + 32 * half + 16 * h), v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        acc[16 * h + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (kLev - l));
+                }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&sm.acc_empty);
+        }
+        if (ok_all) {
+            // W(a, c) = acc 2^(e_a + E_c - 54) (V digits carry 2^(e_a - 47), C digits 2^(E_c - 47), acc 2^-40)
+            const int64_t col = c0 + m;
+            double* out = Wp + (int64_t)blockIdx.y * kOB * nprime;
+            if (col < nprime) {
+                const int ec = E[jc + col];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int a = 32 * half + j;
+                    if (a < nbo) out[(int64_t)a * nprime + col] = ldexp((double)acc[j], ecol[a] + ec - 54);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
     }
 }
 
@@ -780,6 +1019,30 @@ static int make_c_map(CUtensorMap* map, void* A, int64_t lda, int64_t s, int64_t
     return CSLS_OK;
 }
 
+// Tensor map of the int64 trailing matrix for the W = V^T C copies: 16-row (128-byte) x 128-column
+// boxes with the 128-byte swizzle, so the cutters read a column's 16-byte chunks conflict-free.
+static int make_raw_map(CUtensorMap* map, void* A, int64_t lda, int64_t s, int64_t n) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return CSLS_ERR_CUDA;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)s, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)lda * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)kVcRawBox, (cuuint32_t)kVcM};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, A, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return CSLS_ERR_CUDA;
+    return CSLS_OK;
+}
+
 // Column tiles per CTA: the split of each row tile's columns that minimises the waves of
 // one-CTA-per-SM launches times the tiles a CTA walks (plus ~2 tiles for its V planes and the
 // pipeline fill).
@@ -801,46 +1064,35 @@ static int tc_update_cpt(int64_t nrt, int64_t nct, int sms) {
 
 struct EmuScratch {
     int* E;                       // n column exponents
-    unsigned long long* colmax;   // kOB
     int* ecol;                    // kOB
     int* frow;                    // s
-    int* gcol;                    // n
+    int* gsh;                     // n: per-column shift of the update products
     unsigned short* Vd;           // kDig * s * kOB (s rounded up to 128)
     unsigned short* VTd;          // kDig * kOB * s
     unsigned short* Wd;           // kDig * n * kOB (n rounded up to 32)
     double* Wp;                   // split-K partials of W (kOB x n per chunk)
     int64_t wp_elems;
     double* Wn;                   // kOB x n
-    double* T1;                   // first panel's T (32 x 32)
     double* Tb;                   // outer block's T (kOB x kOB)
-    double* gpart;                // Gram partials of the two panels
-    int64_t gparts;
 };
 
-static int64_t emu_wp_elems(int64_t n) {
-    const int64_t a = (int64_t)kOB * (n + kVtcCols);
-    const int64_t b = (int64_t)kOB * kVtcCols * (8LL * device_sm_count() + 8);
-    return a > b ? a : b;
-}
+constexpr int kVcMaxSplit = 16;   // row chunks of W = V^T C (partials kept side by side)
+static int64_t emu_wp_elems(int64_t n) { return (int64_t)kVcMaxSplit * kOB * (n + kVcM); }
 
 static EmuScratch emu_carve(Carve& c, int64_t s, int64_t n) {
     const int64_t ldv = round_up(s, kTcM), ldw = round_up(n, kTcN);
     EmuScratch e;
     e.E = c.take<int>((size_t)n);
-    e.colmax = c.take<unsigned long long>(kOB);
     e.ecol = c.take<int>(kOB);
     e.frow = c.take<int>((size_t)ldv);
-    e.gcol = c.take<int>((size_t)ldw);
+    e.gsh = c.take<int>((size_t)ldw);
     e.Vd = c.take<unsigned short>((size_t)(kDig * ldv * kOB));
     e.VTd = c.take<unsigned short>((size_t)(kDig * ldv * kOB));
     e.Wd = c.take<unsigned short>((size_t)(kDig * ldw * kOB));
     e.wp_elems = emu_wp_elems(n);
     e.Wp = c.take<double>((size_t)e.wp_elems);
     e.Wn = c.take<double>((size_t)(kOB * (n + kOB)));
-    e.T1 = c.take<double>(kPanel * kPanel);
     e.Tb = c.take<double>(kOB * kOB);
-    e.gparts = 2LL * device_sm_count();
-    e.gpart = c.take<double>((size_t)(e.gparts * kPanel * kPanel));
     return e;
 }
 
@@ -849,9 +1101,6 @@ size_t qr_emu_scratch_bytes(int64_t s, int64_t n) {
     emu_carve(c, s, n);
     return c.off;
 }
-
-int qr_panel_launch_f64(double* A, int64_t lda, int64_t s, int64_t j0, int nbw, const QrScratch& q, int* err,
-                        long long spin, cudaStream_t st);
 
 int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, void* emu_work,
                       size_t emu_bytes, int* err, long long spin, cudaStream_t st, int64_t* launches) {
@@ -863,7 +1112,9 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     if ((reinterpret_cast<uintptr_t>(A) & 15) != 0 || (lda & 1) != 0) return CSLS_ERR_ARG;
     CUtensorMap cmap;
     CSLS_TRY(make_c_map(&cmap, A, lda, s, n));
-    CSLS_TRY(raise_smem_limit((const void*)k_emu_vtc, (int)sizeof(VtcSmem)));
+    CUtensorMap rawmap;
+    CSLS_TRY(make_raw_map(&rawmap, A, lda, s, n));
+    CSLS_TRY(raise_smem_limit((const void*)k_emu_vtc_tc, (int)(sizeof(VcSmem) + 1024)));
     CSLS_TRY(raise_smem_limit((const void*)k_emu_update_tc, (int)sizeof(TcUpdSmem)));
     CSLS_TRY(raise_smem_limit((const void*)k_wreduce_ob, (int)kWrSmem));
     const int sms = device_sm_count();
@@ -874,75 +1125,56 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     k_to_fixed<<<fg, 256, 0, st>>>(A, lda, s, n, e.E);
     CSLS_CUDA(cudaGetLastError());
     int64_t nl = 2;
+    const size_t ob_cap = kObSmemCap;
+    CSLS_TRY(raise_smem_limit((const void*)k_obpanel<true>, (int)ob_cap));
     for (int64_t J0 = 0; J0 < n; J0 += kOB) {
         const int nbo = (int)(n - J0 < kOB ? n - J0 : kOB);
-        const int nb1 = nbo < kPanel ? nbo : kPanel;
-        const int nb2 = nbo - nb1;
         const int64_t L = s - J0;
-        // the outer block's columns return to binary64 (rows below and above the diagonal block)
-        dim3 pg((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 256), 256)), (unsigned)nbo);
-        k_panel_to_f64<<<pg, 256, 0, st>>>(A, lda, s, J0, nbo, e.E);
-        CSLS_CUDA(cudaGetLastError());
-        if (J0 > 0) {
-            dim3 tg((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(J0, 256), 64)), (unsigned)nbo);
-            k_panel_top_to_f64<<<tg, 256, 0, st>>>(A, lda, J0, nbo, e.E);
-            CSLS_CUDA(cudaGetLastError());
-        }
-        // first panel, its update of the second one (FP64 MMA), second panel
-        int tk = kt_begin(kFamPanel, st);
-        CSLS_TRY(qr_panel_launch_f64(A, lda, s, J0, nb1, q, err, spin, st));
-        kt_end(tk, 0.0, st);
-        nl += 3;
-        if (nb2 > 0) {
-            CSLS_CUDA(cudaMemcpyAsync(e.T1, q.T, sizeof(double) * kPanel * kPanel, cudaMemcpyDeviceToDevice, st));
-            CSLS_TRY(qr_trailing_update_f64(A, lda, s, J0 + nbo, J0, nb1, q, st));
-            tk = kt_begin(kFamPanel, st);
-            CSLS_TRY(qr_panel_launch_f64(A, lda, s, J0 + kPanel, nb2, q, err, spin, st));
+        const int64_t ldvp = round_up(L, kTcM);   // digit planes use the current block height
+        // the outer block: fixed point -> binary64, Householder factorisation, T, digits of V
+        {
+            int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(L, 128)));
+            int64_t chunk = ceil_div(L, G);
+            G = (int)ceil_div(L, chunk);
+            const size_t smem = (size_t)chunk * nbo * sizeof(double);
+            const bool in_smem = smem <= ob_cap;
+            int64_t J0v = J0, ldav = lda, sv = s, ldvpv = ldvp;
+            int nbov = nbo;
+            long long spinv = spin;
+            double* tau = q.tau;
+            double* part = q.partials;
+            GridBarrier* bar = q.bar;
+            void* args[] = {&A, &ldav, &sv, &J0v, &nbov, &chunk, (void*)&e.E, &tau, (void*)&e.Tb, (void*)&e.Vd,
+                            (void*)&e.VTd, &ldvpv, (void*)&e.frow, (void*)&e.ecol, &part, &bar, &spinv, &err};
+            const int tk = kt_begin(kFamPanel, st);
+            if (in_smem)
+                CSLS_CUDA(cudaLaunchCooperativeKernel((const void*)k_obpanel<true>, dim3(G), dim3(kObThreads), args,
+                                                      smem, st));
+            else
+                CSLS_CUDA(cudaLaunchCooperativeKernel((const void*)k_obpanel<false>, dim3(G), dim3(kObThreads), args,
+                                                      0, st));
             kt_end(tk, 0.0, st);
-            // merged T of the outer block
-            const int64_t L2 = s - J0 - kPanel;
-            int gp = (int)std::min<int64_t>(e.gparts, std::max<int64_t>(1, ceil_div(L2, 128)));
-            const int64_t chunk = round_up(ceil_div(L2, gp), 64);
-            gp = (int)ceil_div(L2, chunk);
-            k_gram12<<<gp, 256, 0, st>>>(A, lda, s, J0, nb2, chunk, e.gpart);
-            CSLS_CUDA(cudaGetLastError());
-            // the partials of each Gram entry summed by a warp (in place into partial 0), so the
-            // single-CTA merge reads one value per entry
-            k_gsum<<<kPanel * kPanel / 8, 256, 0, st>>>(e.gpart, gp);
-            CSLS_CUDA(cudaGetLastError());
-            k_tmerge<<<1, 256, 0, st>>>(e.T1, q.T, e.gpart, 1, nb2, e.Tb);
-            CSLS_CUDA(cudaGetLastError());
-            nl += 6;
-        } else {
-            k_tpad<<<1, 256, 0, st>>>(q.T, e.Tb);
-            CSLS_CUDA(cudaGetLastError());
             nl += 1;
         }
         const int64_t nprime = n - J0 - nbo;
         if (nprime <= 0) continue;
-        // digits of V
-        CSLS_CUDA(cudaMemsetAsync(e.colmax, 0, sizeof(unsigned long long) * kOB, st));
-        k_vcolmax<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L, 4), (int64_t)sms * 4)), 256, 0, st>>>(
-            A, lda, s, J0, nbo, e.colmax);
-        CSLS_CUDA(cudaGetLastError());
-        const int64_t ldvp = round_up(L, kTcM);   // digit planes use the current block height
-        k_vdigits<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ldvp, 256), (int64_t)sms * 8)), 256, 0, st>>>(
-            A, lda, s, J0, nbo, e.colmax, ldvp, e.Vd, e.VTd, e.frow, e.ecol);
-        CSLS_CUDA(cudaGetLastError());
-        // W = V^T C over row chunks
-        const int64_t ntn = ceil_div(nprime, kVtcCols);
-        int64_t ks = ceil_div(8LL * sms, ntn);
-        const int64_t maxks = ceil_div(L, kVtcStep);
-        if (ks > maxks) ks = maxks;
-        if (ks > 64) ks = 64;   // narrow trailing blocks: a few long row chunks keep the partial sums short
-        if (ks < 1) ks = 1;
-        while (ks > 1 && ks * kOB * ntn * kVtcCols > e.wp_elems) --ks;
-        const int64_t kc = round_up(ceil_div(L, ks), kVtcStep);
+        // W = V^T C over row chunks: the split that minimises waves x rows per CTA (plus a fixed
+        // cost of about two K-blocks per CTA), with chunks of at most kVcMaxChunk rows
+        const int64_t ntn = ceil_div(nprime, kVcM);
+        int64_t ks = 1, best = INT64_MAX;
+        for (int64_t k = 1; k <= kVcMaxSplit; ++k) {
+            const int64_t kcb = round_up(ceil_div(L, k), kVcKB);
+            if (kcb > kVcMaxChunk) continue;
+            const int64_t cost = ceil_div(ntn * ceil_div(L, kcb), sms) * (kcb / kVcKB + 2);
+            if (cost < best) { best = cost; ks = k; }
+        }
+        const int64_t kc = round_up(ceil_div(L, ks), kVcKB);
         ks = ceil_div(L, kc);
+        if (kc > kVcMaxChunk || ks > kVcMaxSplit) return CSLS_ERR_ARG;   // rows beyond the accumulator bound
         const double prod_flop = 2.0 * (double)L * (double)nprime * (double)nbo;
-        tk = kt_begin(kFamVtc, st);
-        k_emu_vtc<<<dim3((unsigned)ntn, (unsigned)ks), kEmuThreads, sizeof(VtcSmem), st>>>(
-            reinterpret_cast<const long long*>(A), lda, s, n, J0, nbo, kc, e.VTd, ldvp, e.ecol, e.E, e.Wp, nprime);
+        int tk = kt_begin(kFamVtc, st);
+        k_emu_vtc_tc<<<dim3((unsigned)ntn, (unsigned)ks), kVcThreads, sizeof(VcSmem) + 1024, st>>>(
+            rawmap, e.VTd, J0, nbo, L, kc, e.ecol, e.E, e.Wp, nprime, spin, err);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
         k_wreduce_ob<<<(unsigned)ceil_div(nprime, kWrCols), 256, kWrSmem, st>>>(e.Wp, (int)ks, e.Tb, nbo, e.Wn, nprime);
@@ -950,7 +1182,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         // digits of Wn, then the exact update
         const int64_t ldwp = round_up(nprime, kTcN);
         k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 256)), 256, 0, st>>>(e.Wn, nbo, nprime, ldwp, e.Wd,
-                                                                                        e.gcol);
+                                                                                        e.E, J0 + nbo, e.gsh);
         CSLS_CUDA(cudaGetLastError());
         // a trailing block exists only right of a full 64-column outer block: the update's
         // products always run over K = 64
@@ -959,11 +1191,10 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         const int64_t nrt = ceil_div(L, kTcM), nct = ceil_div(nprime, kTcN);
         const int cpt = tc_update_cpt(nrt, nct, sms);
         k_emu_update_tc<<<dim3((unsigned)ceil_div(nct, cpt), (unsigned)nrt), kTcThreads, sizeof(TcUpdSmem), st>>>(
-            cmap, reinterpret_cast<long long*>(A), lda, s, J0, nbo, e.Vd, e.frow, e.Wd, e.gcol, e.E, nprime, cpt, spin,
-            err);
+            cmap, reinterpret_cast<long long*>(A), lda, s, J0, nbo, e.Vd, e.frow, e.Wd, e.gsh, nprime, cpt, spin, err);
         CSLS_CUDA(cudaGetLastError());
         kt_end(tk, prod_flop, st);
-        nl += 7;
+        nl += 4;
     }
     if (launches) *launches += nl;
     return CSLS_OK;
