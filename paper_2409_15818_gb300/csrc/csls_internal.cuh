@@ -202,6 +202,7 @@ int qr_trailing_update_f64(double* A, int64_t lda, int64_t s, int64_t n_end, int
 // The same factorisation with the trailing-update products emulated exactly on the bf16
 // tensor cores (digit splitting, int64 fixed-point trailing matrix); needs emu scratch.
 size_t qr_emu_scratch_bytes(int64_t s, int64_t n);
+int64_t obpanel_partial_elems(int sms);   // doubles the emulated path's panel needs in QrScratch::partials
 int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScratch& q, void* emu_work,
                       size_t emu_bytes, int* err, long long spin, cudaStream_t st, int64_t* launches);
 // R (n x n, ld n, non-negative diagonal, zero below) from the factored matrix; stats[0..2] =

@@ -588,6 +588,7 @@ QrScratch qr_scratch_carve(Carve& c, int64_t s, int64_t n, int elem_bytes) {
     q.tau = c.take<double>((size_t)n / e + 1);
     q.T = c.take<double>(kPanel * kPanel);
     q.part_elems = (int64_t)device_sm_count() * kPartStride + 8 + kPanel * kPanel;
+    if (obpanel_partial_elems(device_sm_count()) > q.part_elems) q.part_elems = obpanel_partial_elems(device_sm_count());
     q.partials = c.take<double>((size_t)q.part_elems);
     q.wp_elems = wp_capacity(n);
     q.Wp = c.take<double>((size_t)q.wp_elems);

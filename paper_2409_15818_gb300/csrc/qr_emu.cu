@@ -84,6 +84,10 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// An integer-valued float f with |f| <= 2^22, as an int: f + 1.5 x 2^23 lies in [2^23, 2^24], where
+// the float grid is the integers, so its bit pattern is 0x4B400000 + f exactly.
+__device__ __forceinline__ int magic_int(float f) { return __float_as_int(__fadd_rn(f, kMagic)) - kMagicBits; }
+
 // ------------------------------------------------------------------ setup kernels
 
 // E_c = exponent bound of column c of SA: 2^E_c > ||SA(:, c)||_2 >= every |entry| at any later stage.
@@ -239,9 +243,8 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
 // row-scaled (Vd) and column-scaled (VTd) digit planes.
 constexpr int kObThreads = 512;
 constexpr int kObWarps = kObThreads / 32;
-// reduction slots: sigma, alpha, d_k (64), top_k (64), Gram column (64), column max
-constexpr int kRedSig = 0, kRedAlpha = 1, kRedD = 2, kRedTop = 2 + kOB, kRedGram = 2 + 2 * kOB,
-              kRedMax = 2 + 3 * kOB, kRedSlots = 3 + 3 * kOB;
+// reduced values of a step: sigma, alpha, d_k (64), top_k (64)
+constexpr int kRedSig = 0, kRedAlpha = 1, kRedD = 2, kRedTop = 2 + kOB, kRedSlots = 2 + 2 * kOB;
 constexpr size_t kObSmemCap = 180 * 1024;   // dynamic part (the static part is ~41 KB of the 227 KB)
 
 template <bool SMEM>
@@ -265,7 +268,7 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
     int64_t ldw;
     if (SMEM) {
         W = ob_dyn;
-        ldw = chunk;
+        ldw = chunk | 1;   // odd: threads reading the same row of different columns hit different banks
     } else {
         W = A + r0 + J0 * lda;
         ldw = lda;
@@ -288,27 +291,31 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
     __syncthreads();
 
     auto own = [&](int64_t row) { return row >= r0 && row < r1; };
-    // Per step the CTAs exchange (a) summed partials, 128 slots per CTA: sigma (slot 0), d_k (slot k,
-    // k = 1..63), the Gram entries v_a^T v_c (slot 64 + a, a = 0..62) and the column maximum (slot
-    // 127), stored CTA-major so that a reduction reads each CTA's slots contiguously; (b) the owner
-    // CTA's diagonal-row values alpha and top_k (own[0], own[k]), which need no reduction. Both come in
-    // two buffers that alternate by step, so a CTA that runs ahead never overwrites values another
-    // CTA is still reading.
-    constexpr int kSlots = 128, kSlotMax = 127, kSlotGram = 64;
+    // Per step the CTAs exchange (a) summed partials, 64 slots per CTA: sigma (slot 0) and d_k (slot
+    // k, k = 1..63), stored CTA-major so that a reduction reads each CTA's slots contiguously; (b) the
+    // owner CTA's diagonal-row values alpha and top_k (own[0], own[k]), which need no reduction. Both
+    // come in two buffers that alternate by step, so a CTA that runs ahead never overwrites values
+    // another CTA is still reading. The Gram matrix V^T V and the column maxima of V are needed only
+    // once the block is done: they are reduced once at the end.
+    constexpr int kSlots = kOB;
+    constexpr int kGramSlots = kOB * (kOB - 1) / 2 + kOB;   // strict upper Gram entries + column maxima
     double* const own_base = part + 2 * (int64_t)G * kSlots;
+    double* const gram_part = own_base + 2 * (kOB + 1);      // G x kGramSlots, then the reduced entries
+    double* const gram_red = gram_part + (int64_t)G * kGramSlots;
     auto sums = [&](int step) { return part + (int64_t)(step & 1) * G * kSlots + (int64_t)g * kSlots; };
     auto owns = [&](int step) { return own_base + (step & 1) * (kOB + 1); };
-    // two interleaved accumulators per lane, combined in a fixed order
-    auto dot_tail = [&](const double* xs, const double* ys, int rs) {
-        double a0 = 0.0, a1 = 0.0;
-        int r = rs + lane;
-        for (; r + 32 < nloc; r += 64) {
-            a0 += xs[r] * ys[r];
-            a1 += xs[r + 32] * ys[r + 32];
-        }
-        if (r < nloc) a0 += xs[r] * ys[r];
-        double acc = a0 + a1;
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    // Dot products over this CTA's rows: eight threads per product (thread q of the eight takes rows
+    // rs + q, rs + q + 8, ...), combined by three shuffle steps in a fixed order; a warp holds four
+    // products and skips when all four are absent. (FP64 arithmetic is the scarce resource here: each
+    // FP64 warp instruction occupies the pipe for the same time whatever its active lanes, so no warp
+    // computes placeholder products, and a warp per product over a few hundred rows would spend as many
+    // additions on its shuffle tree as on the products.)
+    auto dot8 = [&](const double* xs, const double* ys, int rs, int q) {
+        double acc = 0.0;
+        for (int r = rs + q; r < nloc; r += 8) acc += xs[r] * ys[r];
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
         return acc;
     };
     // partial sums that column c (global row jj = J0 + c) needs, written for step c
@@ -317,63 +324,38 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
         const int rs = (int)(jj + 1 - r0 > 0 ? (jj + 1 - r0 < nloc ? jj + 1 - r0 : nloc) : 0);
         double* ps = sums(c);
         double* po = owns(c);
-        const int ntask = nbo - c;   // task 0: sigma; task t >= 1: d_{c+t}
-        for (int t = warp; t < ntask; t += kObWarps) {
-            const double acc = dot_tail(W + c * ldw, W + (c + t) * ldw, rs);
-            if (lane == 0) {
+        const int ntask = nbo - c;   // task 0: sigma; task t >= 1: d_{c+t}; at most kObThreads / 8
+        const int t = tid >> 3, q = tid & 7;
+        if (warp * 4 < ntask) {   // warp-uniform: some product of this warp is present
+            const bool active = t < ntask;
+            const double acc = dot8(W + c * ldw, W + (c + (active ? t : 0)) * ldw, active ? rs : nloc, q);
+            if (active && q == 0) {
                 ps[t == 0 ? 0 : c + t] = acc;
                 if (own(jj)) po[t == 0 ? 0 : c + t] = W[(c + t) * ldw + (jj - r0)];
             }
         }
     };
-    // Gram column of reflector c (a < c) and its column maximum, written for step c + 1
-    auto gram_sums = [&](int c) {
-        const int64_t jj = J0 + c;
-        const int rs = (int)(jj + 1 - r0 > 0 ? (jj + 1 - r0 < nloc ? jj + 1 - r0 : nloc) : 0);
-        double* ps = sums(c + 1);
-        for (int t = warp; t <= c; t += kObWarps) {
-            const double* vc = W + c * ldw;
-            if (t < c) {
-                double acc = dot_tail(W + t * ldw, vc, rs);
-                if (lane == 0) {
-                    if (own(jj)) acc += W[t * ldw + (jj - r0)];   // v_c = 1 on its diagonal row
-                    ps[kSlotGram + t] = acc;
-                }
-            } else {
-                double mx = 1.0;   // the unit diagonal entry
-                for (int r = rs + lane; r < nloc; r += 32) mx = fmax(mx, fabs(vc[r]));
-                for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                if (lane == 0) ps[kSlotMax] = mx;
-            }
-        }
-    };
-    // Reduction at the barrier of step c: thread (phase h, slot s) sums the slot over CTAs h, h + 4,
-    // ... (independent loads, coalesced across the slots), then the four phases are added in a fixed
-    // order; all CTAs obtain the same bits. Live slots: sigma and d_k (c < k < nbo) for column c,
-    // Gram a < c - 1 and the maximum of reflector c - 1.
-    __shared__ double red4[4][kSlots];
+    // Reduction at the barrier of step c: thread (phase h, slot s) sums the slot over CTAs h, h + 8,
+    // ... (independent loads, coalesced across the slots), then the eight phases are added in a fixed
+    // order; all CTAs obtain the same bits. Live slots: sigma and d_k, c < k < nbo.
+    __shared__ double red8[8][kSlots];
     auto reduce_step = [&](int c) {
-        const int sl = tid & (kSlots - 1), h = tid >> 7;
-        const bool live = (sl == 0 && c < nbo) || (sl >= 1 && sl < kOB && sl > c && sl < nbo) ||
-                          (sl >= kSlotGram && sl < kSlotMax && sl - kSlotGram < c - 1) || (sl == kSlotMax && c >= 1);
+        const int sl = tid & (kSlots - 1), h = tid >> 6;
+        const bool live = sl == 0 || (sl > c && sl < nbo);
         double acc = 0.0;
         if (live) {
             const double* src = part + (int64_t)(c & 1) * G * kSlots + sl;
-            if (sl == kSlotMax)
-                for (int q = h; q < G; q += 4) acc = fmax(acc, __ldcg(src + (int64_t)q * kSlots));
-            else
-                for (int q = h; q < G; q += 4) acc += __ldcg(src + (int64_t)q * kSlots);
+            for (int q = h; q < G; q += 8) acc += __ldcg(src + (int64_t)q * kSlots);
         }
-        red4[h][sl] = acc;
+        red8[h][sl] = acc;
         __syncthreads();
         if (tid < kSlots) {
-            const double v = tid == kSlotMax ? fmax(fmax(red4[0][tid], red4[1][tid]), fmax(red4[2][tid], red4[3][tid]))
-                                             : ((red4[0][tid] + red4[1][tid]) + red4[2][tid]) + red4[3][tid];
+            double v = red8[0][tid];
+#pragma unroll
+            for (int i = 1; i < 8; ++i) v += red8[i][tid];
             if (tid == 0) red[kRedSig] = v;
-            else if (tid < kOB) red[kRedD + tid] = v;
-            else if (tid < kSlotMax) red[kRedGram + tid - kSlotGram] = v;
-            else red[kRedMax] = v;
-        } else if (tid < kSlots + kOB && c < nbo) {
+            else red[kRedD + tid] = v;
+        } else if (tid < kSlots + kOB) {
             const int k = tid - kSlots;   // owner values of column c
             const double v = __ldcg(owns(c) + k);
             if (k == 0) red[kRedAlpha] = v;
@@ -382,31 +364,33 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
     };
 
     column_sums(0);
-    for (int c = 0; c <= nbo; ++c) {
+    for (int c = 0; c < nbo; ++c) {
         if (!grid_sync(bar, G, spin, err)) return;
         reduce_step(c);
         __syncthreads();
-        if (c >= 1) {   // Gram column and maximum of reflector c - 1
-            for (int a = tid; a < c - 1; a += kObThreads) gT[a + (c - 1) * kOB] = red[kRedGram + a];
-            if (tid == 0) cmax[c - 1] = red[kRedMax];
-        }
-        if (c == nbo) break;
         const int64_t jj = J0 + c;
-        // reflector of column c (every thread forms the same scalars)
-        const double sigma = red[kRedSig], alpha = red[kRedAlpha];
-        double tau_c = 0.0, scal = 1.0, beta = alpha;
-        const bool live = sigma != 0.0;
-        if (live) {
-            const double nrm = sqrt(alpha * alpha + sigma);
-            beta = alpha >= 0.0 ? -nrm : nrm;
-            tau_c = (beta - alpha) / beta;
-            scal = 1.0 / (alpha - beta);
-        }
-        if (tid < kOB) wk[tid] = (tid > c && tid < nbo) ? tau_c * (red[kRedTop + tid] + scal * red[kRedD + tid]) : 0.0;
+        // reflector of column c: one thread forms the scalars (FP64 division and square root are
+        // expensive on this part, so they are not repeated per thread)
+        __shared__ double refl[3];   // tau, 1 / (alpha - beta), beta
         if (tid == 0) {
+            const double sigma = red[kRedSig], alpha = red[kRedAlpha];
+            double tau_c = 0.0, scal = 1.0, beta = alpha;
+            if (sigma != 0.0) {
+                const double nrm = sqrt(alpha * alpha + sigma);
+                beta = alpha >= 0.0 ? -nrm : nrm;
+                tau_c = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            refl[0] = tau_c;
+            refl[1] = scal;
+            refl[2] = beta;
             taus[c] = tau_c;
             if (g == 0) tau[jj] = tau_c;
         }
+        __syncthreads();
+        const double tau_c = refl[0], scal = refl[1], beta = refl[2];
+        const bool live = red[kRedSig] != 0.0;
+        if (tid < kOB) wk[tid] = (tid > c && tid < nbo) ? tau_c * (red[kRedTop + tid] + scal * red[kRedD + tid]) : 0.0;
         const int rj = (int)(jj - r0);   // local index of the diagonal row (may be outside [0, nloc))
         if (live) {
             for (int r = tid; r < nloc; r += kObThreads) {
@@ -427,11 +411,82 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
         }
         __syncthreads();
         if (c + 1 < nbo) column_sums(c + 1);
-        gram_sums(c);
-        __syncthreads();
     }
-    // T of the block (CTA 0)
+    // Gram matrix of V (entries a < b over this CTA's rows, v masked: 0 above its diagonal row, 1 on
+    // it) and the column maxima of |v|, a warp per entry
+    {
+        double* gp = gram_part + (int64_t)g * kGramSlots;
+        // strict upper entries, four threads per entry: e -> (a, b), a < b, b (b - 1) / 2 <= e < b (b + 1) / 2
+        const int ngram = kGramSlots - kOB;
+        for (int e0 = 0; e0 < ngram; e0 += kObThreads / 4) {
+            const int e = e0 + (tid >> 2), q = tid & 3;
+            const bool active = e < ngram;
+            int bcol = 1, acol = 0;
+            if (active) {
+                bcol = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
+                while (bcol * (bcol - 1) / 2 > e) --bcol;
+                while ((bcol + 1) * bcol / 2 <= e) ++bcol;
+                acol = e - bcol * (bcol - 1) / 2;
+            }
+            const bool real = active && bcol < nbo;
+            const int64_t db = J0 + (real ? bcol : 0);   // rows >= db carry v_b (1 on db)
+            const int rs = real ? (int)(db - r0 > 0 ? (db - r0 < nloc ? db - r0 : nloc) : 0) : nloc;
+            const int rd = (int)(db - r0);
+            const double* va = W + (real ? acol : 0) * ldw;
+            const double* vb = W + (real ? bcol : 0) * ldw;
+            double a0 = 0.0, a1 = 0.0;
+            int r = rs + q;
+            for (; r + 4 < nloc; r += 8) {
+                a0 += va[r] * (r == rd ? 1.0 : vb[r]);
+                a1 += va[r + 4] * (r + 4 == rd ? 1.0 : vb[r + 4]);
+            }
+            if (r < nloc) a0 += va[r] * (r == rd ? 1.0 : vb[r]);
+            double acc = a0 + a1;
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (active && q == 0) gp[e] = real ? acc : 0.0;
+        }
+        for (int e = ngram + warp; e < kGramSlots; e += kObWarps) {
+            {
+                const int a = e - (kGramSlots - kOB);
+                double mx = a < nbo ? 1.0 : 0.0;   // the unit diagonal entry
+                if (a < nbo) {
+                    const int64_t da = J0 + a;
+                    const int rs = (int)(da + 1 - r0 > 0 ? (da + 1 - r0 < nloc ? da + 1 - r0 : nloc) : 0);
+                    for (int r = rs + lane; r < nloc; r += 32) mx = fmax(mx, fabs(W[a * ldw + r]));
+                }
+                for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (lane == 0) gp[e] = mx;
+            }
+        }
+    }
+    if (!grid_sync(bar, G, spin, err)) return;
+    // each CTA reduces a share of the entries over the G partials (fixed order), then all CTAs take
+    // the column maxima and CTA 0 the Gram matrix
+    for (int e = g * kObWarps + warp; e < kGramSlots; e += G * kObWarps) {
+        double acc = 0.0;
+        const bool is_max = e >= kGramSlots - kOB;
+        for (int q = lane; q < G; q += 32) {
+            const double v = __ldcg(gram_part + (int64_t)q * kGramSlots + e);
+            acc = is_max ? fmax(acc, v) : acc + v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_xor_sync(0xffffffffu, acc, o);
+            acc = is_max ? fmax(acc, v) : acc + v;
+        }
+        if (lane == 0) gram_red[e] = acc;
+    }
+    if (!grid_sync(bar, G, spin, err)) return;
+    if (tid < kOB) cmax[tid] = __ldcg(gram_red + (kGramSlots - kOB) + tid);
+    // T of the block (CTA 0): T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) (V^T V)(0:i, i)
     if (g == 0) {
+        for (int e = tid; e < kGramSlots - kOB; e += kObThreads) {
+            int bcol = (int)((1.0 + sqrt(1.0 + 8.0 * (double)e)) * 0.5);
+            while (bcol * (bcol - 1) / 2 > e) --bcol;
+            while ((bcol + 1) * bcol / 2 <= e) ++bcol;
+            gT[(e - bcol * (bcol - 1) / 2) + bcol * kOB] = __ldcg(gram_red + e);
+        }
+        __syncthreads();
         for (int i = 0; i < nbo; ++i) {
             double v = 0.0;
             if (tid < i) {
@@ -449,6 +504,7 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
             Tb[i] = (a <= b && b < nbo) ? gT[i] : 0.0;
         }
     }
+    __syncthreads();
     // column exponents of V (for V^T C) and the digits of this CTA's rows
     __shared__ int ecol_s[kOB];
     if (tid < kOB) {
@@ -706,11 +762,13 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                 const int64_t col = cbase + j;
                 if (rok && col < nprime) {
                     // acc = sum_l T_l 256^(5 - l): T_0 256 + T_1 fits 32 bits (|T_0| <= 64 x 2^14), the
-                    // rest is three 32 x 32 -> 64-bit multiply-adds
-                    const int t0 = __float2int_rn(__uint_as_float(v[0][j]));
-                    const int t1 = __float2int_rn(__uint_as_float(v[1][j]));
-                    const int t2 = __float2int_rn(__uint_as_float(v[2][j]));
-                    const int t3 = __float2int_rn(__uint_as_float(v[3][j]));
+                    // rest is three 32 x 32 -> 64-bit multiply-adds. Levels 0..3 have at most 4 digit
+                    // pairs, |T_l| <= 4 x 64 x 2^14 = 2^22, and are read by the magic-number add (one
+                    // FP32 add, one integer subtract); levels 4 and 5 by a conversion instruction.
+                    const int t0 = magic_int(__uint_as_float(v[0][j]));
+                    const int t1 = magic_int(__uint_as_float(v[1][j]));
+                    const int t2 = magic_int(__uint_as_float(v[2][j]));
+                    const int t3 = magic_int(__uint_as_float(v[3][j]));
                     const int t4 = __float2int_rn(__uint_as_float(v[4][j]));
                     const int t5 = __float2int_rn(__uint_as_float(v[5][j]));
                     long long acc = (long long)t2 * (1LL << 24) + ((long long)t3 * 65536 + ((long long)t4 * 256 + t5));
@@ -967,9 +1025,16 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
                     uint32_t v[16];
                     tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kOB * l + 32 * half + 16 * h), v);
                     tc::tmem_ld_wait();
+                    // levels 0 and 1 hold at most 2 x 128 x 2^14 = 2^22 per window: magic-number read
+                    if (l <= 1) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        acc[16 * h + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (kLev - l));
+                        for (int j = 0; j < 16; ++j)
+                            acc[16 * h + j] += (long long)magic_int(__uint_as_float(v[j])) << (8 * (kLev - l));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            acc[16 * h + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (kLev - l));
+                    }
                 }
             tc::fence_before_sync();
             tc::mbar_arrive(&sm.acc_empty);
@@ -1096,6 +1161,13 @@ static EmuScratch emu_carve(Carve& c, int64_t s, int64_t n) {
     return e;
 }
 
+// doubles of the panel's exchange buffer: per-step slots (two buffers), owner values, the Gram
+// partials of every CTA and their reduction
+int64_t obpanel_partial_elems(int sms) {
+    const int64_t gram = kOB * (kOB - 1) / 2 + kOB;
+    return (int64_t)sms * (2 * kOB + gram) + 2 * (kOB + 1) + gram + 64;
+}
+
 size_t qr_emu_scratch_bytes(int64_t s, int64_t n) {
     Carve c{nullptr, 0, 0, true};
     emu_carve(c, s, n);
@@ -1136,7 +1208,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
             int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(L, 128)));
             int64_t chunk = ceil_div(L, G);
             G = (int)ceil_div(L, chunk);
-            const size_t smem = (size_t)chunk * nbo * sizeof(double);
+            const size_t smem = (size_t)(chunk | 1) * nbo * sizeof(double);
             const bool in_smem = smem <= ob_cap;
             int64_t J0v = J0, ldav = lda, sv = s, ldvpv = ldvp;
             int nbov = nbo;
