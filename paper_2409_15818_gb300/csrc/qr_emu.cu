@@ -75,6 +75,29 @@ __device__ __forceinline__ void digits_fix(long long c, int (&d)[kDig]) {
     cut_digits(N, d);
 }
 
+// The six digits of a fixed-point entry (|Cfix| < 2^62) as floats, the same digits as digits_fix:
+// after adding 128 to each of the five low bytes of N, byte b of the sum is digit + 128, and one
+// byte permute places it under the exponent of 2^23 (the float 2^23 + byte), so one FP32 subtract
+// gives the digit exactly; the top digit is the sum shifted right by 40.
+__device__ __forceinline__ void digit_floats_fix(long long c, float (&f)[kDig]) {
+    const long long M = ((c + (1LL << (kFixBits - kNumBits - 1))) >> (kFixBits - kNumBits)) + 0x8080808080LL;
+    const uint32_t lo = (uint32_t)M, hi = (uint32_t)(M >> 32);
+    const float base = 8388736.0f;   // 2^23 + 128
+    f[5] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7540)) - base;
+    f[4] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7541)) - base;
+    f[3] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7542)) - base;
+    f[2] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7543)) - base;
+    f[1] = __uint_as_float(__byte_perm(hi, 0x4B000000u, 0x7540)) - base;
+    f[0] = __int_as_float(kMagicBits + ((int)hi >> 8)) - kMagic;
+}
+
+// two floats holding small integers (exact in bf16) as one bf16x2 word: lo in bits 0..15
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 __device__ __forceinline__ unsigned short bf16_of_int(int v) {
     // |v| <= 128: exactly representable. int -> float by the same magic-number trick
     // (one integer add, one float subtract), then the top 16 bits are the bf16 pattern.
@@ -574,9 +597,9 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
 //                        covers the levels p .. 5 (Wn planes stacked along N); two accumulator
 //                        sets of 6 x 32 columns, so the MMAs of tile i + 1 run while tile i is
 //                        written back;
-//   warps 2..9           epilogue: TMEM -> registers, levels combined in int64, scaled onto the
+//   warps 2..17          epilogue: TMEM -> registers, levels combined in int64, scaled onto the
 //                        column's fixed-point grid and added to the staged C entry; one thread
-//                        per row and 16 columns, so each column store of a warp is 256
+//                        per row and 8 columns, so each column store of a warp is 256
 //                        contiguous bytes.
 // Every wait is bounded (spin polls and 2 s of wall time); a role that gives up sets the CTA's
 // abort flag and the error word, and the CTA still waits for its copies and MMAs in flight and
@@ -586,7 +609,8 @@ constexpr int kTcPlaneA = kTcM * kOB * 2;        // bytes of one V digit plane t
 constexpr int kTcPlaneB = kTcN * kOB * 2;        // bytes of one Wn digit plane tile (4 KB)
 constexpr int kTcBufCols = kTcLevels * kTcN;     // TMEM columns of one accumulator set (192)
 constexpr int kTcTmemCols = 512;
-constexpr int kTcEpiWarps = 8;
+constexpr int kTcEpiWarps = 16;
+constexpr int kTcEpiCols = kTcN / (kTcEpiWarps / 4);   // columns of a tile per epilogue warp (8)
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
 constexpr unsigned long long kTcWaitNs = 2000000000ULL;
 constexpr long long kTeardownSpin = 1LL << 62;   // teardown waits: bounded by kTcWaitNs alone
@@ -733,11 +757,12 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
         __syncwarp();
     } else {
         const int quarter = warp & 3;              // a warp reads TMEM lanes 32 (warp % 4) .. + 31
-        const int half = (warp - 2) >> 2;          // columns 16 half .. + 15 of each tile
+        const int part = (warp - 2) >> 2;          // columns kTcEpiCols part .. + kTcEpiCols - 1 of each tile
         const int r = quarter * 32 + lane;
         const int64_t lr = rb + r;
         const bool rok = lr < L;
         const int fr = rok ? frow[lr] : 0;
+        long long* const crow = Cfix + (J0 + lr) + jc * lda;   // this thread's row of the trailing block
         for (int i = 0; i < ntile; ++i) {
             const int b = i & 1, u = i >> 1;
             bool ok = tc::mbar_wait(&sm.done[b], u & 1, spin, kTcWaitNs, abort) &&
@@ -749,16 +774,17 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                 break;
             }
             tc::fence_after_sync();
-            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTcBufCols + half * 16);
-            uint32_t v[kTcLevels][16];
+            const uint32_t ta =
+                tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTcBufCols + part * kTcEpiCols);
+            uint32_t v[kTcLevels][kTcEpiCols];
 #pragma unroll
-            for (int l = 0; l < kTcLevels; ++l) tc::tmem_ld16(ta + l * kTcN, v[l]);
+            for (int l = 0; l < kTcLevels; ++l) tc::tmem_ld8(ta + l * kTcN, v[l]);
             tc::tmem_ld_wait();
             tc::fence_before_sync();
             tc::mbar_arrive(&sm.tfree[b]);   // the accumulator set may take tile i + 2's MMAs now
-            const int64_t cbase = (ct0 + i) * kTcN + half * 16;
+            const int64_t cbase = (ct0 + i) * kTcN + part * kTcEpiCols;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < kTcEpiCols; ++j) {
                 const int64_t col = cbase + j;
                 if (rok && col < nprime) {
                     // acc = sum_l T_l 256^(5 - l): T_0 256 + T_1 fits 32 bits (|T_0| <= 64 x 2^14), the
@@ -778,7 +804,7 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                     long long dlt;
                     if (sh >= 0) dlt = sh < 63 ? acc << sh : 0;
                     else dlt = -sh < 63 ? (acc + (1LL << (-sh - 1))) >> (-sh) : 0;
-                    Cfix[(J0 + lr) + (jc + col) * lda] = sm.C[b][half * 16 + j][r] + dlt;
+                    crow[col * lda] = sm.C[b][part * kTcEpiCols + j][r] + dlt;
                 }
             }
             tc::mbar_arrive(&sm.freed[b]);
@@ -981,15 +1007,12 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
                 }
                 uint32_t pk[kDig][4];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    int d[kDig];
-                    digits_fix(cv[e], d);
+                for (int e = 0; e < 8; e += 2) {
+                    float f0[kDig], f1[kDig];
+                    digit_floats_fix(cv[e], f0);
+                    digit_floats_fix(cv[e + 1], f1);
 #pragma unroll
-                    for (int q = 0; q < kDig; ++q) {
-                        const uint32_t h = bf16_of_int(d[q]);
-                        if (e & 1) pk[q][e >> 1] |= h << 16;
-                        else pk[q][e >> 1] = h;
-                    }
+                    for (int q = 0; q < kDig; ++q) pk[q][e >> 1] = pack_bf16x2(f0[q], f1[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < kDig; ++q)
