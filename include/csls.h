@@ -94,11 +94,18 @@ typedef struct {
                              side): it solves for the correction from r0 = b - A x, keeps ||b|| in
                              the stopping rule, and returns x + correction. Use with the x0 of
                              csls_factor_warm (Remark 3.1) or any other initial guess. */
+    int64_t refine;       /* restarts after the solve (single right-hand-side path): LSQR is run again
+                             from the x just found, on the correction from r = b - A x, recomputed in
+                             binary64 (the warm start above with x0 = the previous solution). With
+                             per-step triangular solves the first solve's attainable accuracy in the
+                             A-norm is limited by rounding in the preconditioner applications, relative
+                             to the size of the iterates; the restart solves for a small correction, so
+                             one restart brings x to the accuracy of the residual computation. 0 = none. */
 } csls_opts;
 
 /* Defaults: gamma 4, s 0, seed 1, QR, F64, rcond 0, atol = btol = 1e-12,
  * maxit 0 (= n), fixed_iters 0, guard_cond 10, spin_limit 2e7, check_every 16, time_kernels 0,
- * warm_start 0. */
+ * warm_start 0, refine 0. */
 void csls_opts_default(csls_opts* opts);
 
 /* Host-side report, filled by csls_factor / csls_solve / csls_solve_backward. */
@@ -123,6 +130,8 @@ typedef struct {
     double kern_ms[3];
     int64_t kern_launches[3];
     double kern_flop[3];
+    int64_t iterations_refine;   /* csls_solve with opts->refine: iterations of the restarts (included in
+                                    `iterations`) */
 } csls_report;
 
 typedef struct csls_factor_s csls_factor_t;

@@ -314,9 +314,11 @@ def explicit_lsqr(A, b, fac, tol=1e-12, maxit=None, fixed_iters=0):
 
 
 def csqrp_lsqr(A, b, gamma=4.0, s=None, seed=1, variant="qr", prec="f64", tol=1e-12, maxit=None,
-               fixed_iters=0, history=False, warm=False):
+               fixed_iters=0, history=False, warm=False, refine=0):
     """Full CSQRP-LSQR (Algorithm 1) / CSSVDP-LSQR (Algorithm 2) in the implicit form; with warm=True
-    LSQR starts from the sketch-and-solve point of Remark 3.1."""
+    LSQR starts from the sketch-and-solve point of Remark 3.1. refine > 0 restarts LSQR that many times
+    from the solution found (the same initial-point form, x0 = the previous x): each restart solves for
+    the correction from r = b - A x. info["iterations_refine"] counts the restarts' iterations."""
     s = sketch_size(A, gamma, s)
     fac = factor(A, s, seed, variant, prec)
     x0 = None
@@ -325,4 +327,12 @@ def csqrp_lsqr(A, b, gamma=4.0, s=None, seed=1, variant="qr", prec="f64", tol=1e
         fac = dict(fac, x0=x0)
     res = lsqr(A, b, fac["F"], fac["kind"], atol=tol, btol=tol, maxit=maxit, fixed_iters=fixed_iters,
                history=history, x0=x0)
+    if refine > 0:
+        x, info = res[0], dict(res[1])
+        its = 0
+        for _ in range(refine):
+            x, inf2 = lsqr(A, b, fac["F"], fac["kind"], atol=tol, btol=tol, maxit=maxit, x0=x)
+            its += inf2["iterations"]
+        info.update(iterations_refine=its, rnorm=inf2["rnorm"], istop=inf2["istop"])
+        res = (x, info) + tuple(res[2:])
     return (fac,) + tuple(res)

@@ -39,7 +39,8 @@ class csls_opts(ctypes.Structure):
                 ("variant", ctypes.c_int), ("factor_prec", ctypes.c_int), ("rcond", ctypes.c_double),
                 ("atol", ctypes.c_double), ("btol", ctypes.c_double), ("maxit", ctypes.c_int64),
                 ("fixed_iters", ctypes.c_int64), ("guard_cond", ctypes.c_double), ("spin_limit", ctypes.c_int64),
-                ("check_every", ctypes.c_int64), ("time_kernels", ctypes.c_int64), ("warm_start", ctypes.c_int64)]
+                ("check_every", ctypes.c_int64), ("time_kernels", ctypes.c_int64), ("warm_start", ctypes.c_int64),
+                ("refine", ctypes.c_int64)]
 
 
 class csls_report(ctypes.Structure):
@@ -50,7 +51,7 @@ class csls_report(ctypes.Structure):
                 ("rdiag_max", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_factor", ctypes.c_double),
                 ("ms_solve", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("kern_ms", ctypes.c_double * 3), ("kern_launches", ctypes.c_int64 * 3),
-                ("kern_flop", ctypes.c_double * 3)]
+                ("kern_flop", ctypes.c_double * 3), ("iterations_refine", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -185,7 +186,7 @@ class Csr:
 
 def make_opts(gamma=4.0, s=0, seed=1, variant="qr", prec="f64", rcond=0.0, atol=1e-12, btol=1e-12, maxit=0,
               fixed_iters=0, guard_cond=10.0, spin_limit=20_000_000, check_every=16, time_kernels=0, warm_start=0,
-              tol=None):
+              refine=0, tol=None):
     o = csls_opts()
     _lib().csls_opts_default(ctypes.byref(o))
     if tol is not None:
@@ -197,6 +198,7 @@ def make_opts(gamma=4.0, s=0, seed=1, variant="qr", prec="f64", rcond=0.0, atol=
     o.guard_cond, o.spin_limit, o.check_every = float(guard_cond), int(spin_limit), int(check_every)
     o.time_kernels = int(time_kernels)
     o.warm_start = int(warm_start)
+    o.refine = int(refine)
     return o
 
 

@@ -402,6 +402,8 @@ void csls_opts_default(csls_opts* o) {
     o->time_kernels = 0;
     o->spin_limit = 20000000;
     o->check_every = 16;
+    o->warm_start = 0;
+    o->refine = 0;
 }
 
 int csls_sketch_workspace(const csls_csr* A, int64_t s, size_t* bytes) {
@@ -690,15 +692,30 @@ int csls_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64
         for (int64_t k = 0; k < nrhs; ++k) {
             csls_report rk{};
             int sk = solve_one(F, A, b + k * ldb, x + k * ldx, o, w, &rk, st, &launches);
+            int64_t its = rk.iterations, its_ref = 0;
+            // restarts: LSQR again from the x just found, on the correction from r = b - A x
+            csls_opts orf = *o;
+            orf.warm_start = 1;
+            for (int64_t p = 0; p < o->refine && (sk == CSLS_OK || sk == CSLS_ERR_NOT_CONVERGED); ++p) {
+                csls_report rr{};
+                sk = solve_one(F, A, b + k * ldb, x + k * ldx, &orf, w, &rr, st, &launches);
+                its_ref += rr.iterations;
+                rr.bnorm = rk.bnorm;   // of the original right-hand side
+                rr.cond_est = std::max(rr.cond_est, rk.cond_est);   // the longer bidiagonal bounds it better
+                rk = rr;
+            }
+            its += its_ref;
+            rk.iterations = its;
+            rk.iterations_refine = its_ref;
             if (k == 0 && rep) *rep = rk;
-            max_it = std::max<int64_t>(max_it, rk.iterations);
+            max_it = std::max<int64_t>(max_it, its);
             if (status == CSLS_OK && sk != CSLS_OK) status = sk;
             if (sk == CSLS_ERR_CUDA || sk == CSLS_ERR_TIMEOUT) break;
         }
     }
     const double ms = t.stop();
     if (rep) {
-        rep->iterations = max_it;
+        rep->iterations = max_it;   // first right-hand side's refine count stays as reported
         rep->ms_solve = ms;
         rep->launches = launches;
         rep->s = F->s;

@@ -14,7 +14,11 @@ solves):
   * x_floor<seed>: LSQR run for a fixed number of iterations far past convergence,
                    at the floating-point floor of the iteration (the best estimate
                    of x_* = argmin ||Ax - b|| the oracle can give);
-  * hist<seed>:    the ||r_k|| estimates of the tol run.
+  * hist<seed>:    the ||r_k|| estimates of the tol run;
+  * x_ref<seed>:   LSQR restarted once from x_tol<seed> (the correction from r = b - A x, same
+                   stopping rule): per-step triangular solves limit the first solve's attainable
+                   A-norm accuracy (its floor moves with the sketch by ~1e-9 on the 2D bench
+                   workload); the restart removes that limit.
 With --hhqr it also stores x_hh, the dense Householder least-squares solution (the
 HHQR direct method of Section 4.1), an estimate of x_* by an independent route.
 
@@ -22,6 +26,7 @@ The spread between these estimates (two sketches, and the direct solve) is the
 problem's own floating-point spread in the A-norm that Theorem 3.3 controls.
 
 Usage: python tests/golden/make_oracle_cache.py --config cfg2 --seeds 1 2 [--hhqr] [--threads 8]
+(A run resumes from the stored file: results already present for the same inputs are kept.)
 """
 import argparse
 import hashlib
@@ -69,26 +74,34 @@ def main():
                 if k.startswith(("x_", "hist", "it_", "istop_", "rnorm_", "secs_")):
                     res[k] = v
     for seed in args.seeds:
-        if "x_floor%d" % seed in res:
+        if all(("%s%d" % (k, seed)) in res for k in ("x_tol", "x_floor", "x_ref")):
             continue
         t0 = time.time()
         fac = oracle.factor(p, s, seed)
         t1 = time.time()
         R = fac["R"]
         fac = None
-        x_tol, info, hist = oracle.lsqr(p, b, R, atol=args.tol, btol=args.tol, history=True)
-        x_fl, info_fl = oracle.lsqr(p, b, R, fixed_iters=args.floor_iters)
+        if "x_floor%d" % seed not in res:
+            x_tol, info, hist = oracle.lsqr(p, b, R, atol=args.tol, btol=args.tol, history=True)
+            x_fl, info_fl = oracle.lsqr(p, b, R, fixed_iters=args.floor_iters)
+            res["x_tol%d" % seed] = x_tol
+            res["x_floor%d" % seed] = x_fl
+            res["hist%d" % seed] = hist
+            res["it_tol%d" % seed] = info["iterations"]
+            res["istop_tol%d" % seed] = info["istop"]
+            res["rnorm_floor%d" % seed] = float(np.linalg.norm(b - oracle.spmv(p, x_fl)))
         t2 = time.time()
-        res["x_tol%d" % seed] = x_tol
-        res["x_floor%d" % seed] = x_fl
-        res["hist%d" % seed] = hist
-        res["it_tol%d" % seed] = info["iterations"]
-        res["istop_tol%d" % seed] = info["istop"]
-        res["rnorm_floor%d" % seed] = float(np.linalg.norm(b - oracle.spmv(p, x_fl)))
+        # one restart from the tol-stopped solution (the correction from r = b - A x), same rule
+        x_ref, info_ref = oracle.lsqr(p, b, R, atol=args.tol, btol=args.tol, x0=res["x_tol%d" % seed])
+        t3 = time.time()
+        res["x_ref%d" % seed] = x_ref
+        res["it_ref%d" % seed] = info_ref["iterations"]
         res["secs_factor%d" % seed] = t1 - t0
-        res["secs_lsqr%d" % seed] = t2 - t1
-        print("seed %d: factor %.0f s, lsqr %.0f s, %d iterations (istop %d), A-norm(tol vs floor) %.3e"
-              % (seed, t1 - t0, t2 - t1, info["iterations"], info["istop"], a_norm_rel(p, x_tol, x_fl)), flush=True)
+        res["secs_lsqr%d" % seed] = t3 - t1
+        print("seed %d: factor %.0f s, lsqr %.0f s, %d + %d iterations, A-norm(tol vs floor) %.3e, (restart vs floor) "
+              "%.3e" % (seed, t1 - t0, t3 - t1, int(res["it_tol%d" % seed]), info_ref["iterations"],
+                        a_norm_rel(p, res["x_tol%d" % seed], res["x_floor%d" % seed]),
+                        a_norm_rel(p, x_ref, res["x_floor%d" % seed])), flush=True)
         np.savez_compressed(out, **res)
     if args.hhqr and "x_hh" not in res:
         t0 = time.time()

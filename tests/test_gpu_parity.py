@@ -160,6 +160,48 @@ def test_solve_rfm_matches_oracle(csls, case):
     assert rep["istop"] in (1, 2) and rep["cond_est"] < 10
 
 
+@pytest.mark.parametrize("case", ["cfg1", "ragged_rfm"])
+@pytest.mark.parametrize("prec", ["f64", "f64emu"])
+def test_restarted_solve_matches_oracle(csls, case, prec):
+    """One LSQR restart from the solution found (the correction from r = b - A x): the GPU's restarted
+    solution equals the oracle's restarted one in the A-norm to 1e-10, and both are at least as close
+    to the dense Householder solution as the first solves are."""
+    p = SKETCH_CASES[case]()
+    Ad = p.dense()
+    b = p.b[0]
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=11, prec=prec)
+    x1, rep1 = csls.csls_solve(F, A, torch.tensor(b, device="cuda"))
+    x, rep = csls.csls_solve(F, A, torch.tensor(b, device="cuda"), refine=1)
+    x1, x = x1.cpu().numpy(), x.cpu().numpy()
+    assert rep["iterations_refine"] > 0 and rep["iterations"] == rep1["iterations"] + rep["iterations_refine"]
+    _, xo, info = oracle.csqrp_lsqr(p, b, seed=11, refine=1)
+    assert info["iterations_refine"] > 0
+    x_hh, _ = oracle.hhqr_solve(Ad, b)
+    assert _anorm_rel(Ad, x, xo) <= 1e-10
+    assert _anorm_rel(Ad, x, x_hh) <= max(2e-12, 2 * _anorm_rel(Ad, x1, x_hh))
+    assert abs(rep["rnorm"] - np.linalg.norm(b - Ad @ x)) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_restart_removes_the_sketch_dependence(csls):
+    """On a 3x3-box RFM system (cond(A) ~ 1e9) the first solves with two different sketches end
+    ~1e-10 apart in the A-norm (the implicit form's rounding floor moves with R); after one restart
+    they agree to 1e-12 and sit within 1e-11 of the dense Householder solution."""
+    p = poisson2d(3, 3, 150, 25, 25, R=2.0, seed=2)     # 6,525 x 1,350
+    Ad = p.dense()
+    b = p.b[0]
+    A = dev(csls, p)
+    xs = []
+    for seed in (1, 2):
+        F = csls.csls_factor(A, seed=seed, prec="f64emu")
+        x, rep = csls.csls_solve(F, A, torch.tensor(b, device="cuda"), refine=1)
+        xs.append(x.cpu().numpy())
+    x_hh, _ = oracle.hhqr_solve(Ad, b)
+    assert _anorm_rel(Ad, xs[0], xs[1]) <= 1e-12
+    for x in xs:
+        assert _anorm_rel(Ad, x, x_hh) <= 1e-11
+
+
 def test_fixed_iterations_track_oracle(csls):
     """Early iterates match the oracle's when both preconditioners agree to
     rounding (a well-conditioned sketch; on the RFM sketches the two R factors
