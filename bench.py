@@ -52,6 +52,9 @@ def parse():
                     help="start LSQR from the sketch-and-solve point R^-1 Q^T S b (Remark 3.1)")
     ap.add_argument("--variant", default="qr", choices=["qr", "svd"],
                     help="preconditioner: QR of the sketch (Algorithm 1) or truncated SVD (Algorithm 2)")
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="LSQR stopping tolerance atol = btol (the tau of Section 4.1); with one restart the "
+                         "A-norm accuracy is far below it (the first solve stops at its rounding floor anyway)")
     ap.add_argument("--refine", type=int, default=1,
                     help="LSQR restarts from the solution found (correction from r = b - A x); the first solve's "
                          "A-norm accuracy is limited by the per-step triangular solves, one restart removes that")
@@ -350,7 +353,7 @@ def main():
                     "rank=%d nnz=%d, b = A x_true" % (args.config[3:], m, n, p.info["rank"], nnz))
     A = csls.Csr.from_numpy(p.row_ptr, p.col, p.val, m, n)
     b = torch.tensor(p.b[0] if p.nrhs == 1 else p.b, device="cuda")   # cfg4a: 64 right-hand sides
-    opts = dict(seed=1, prec=args.prec, tol=1e-12, variant=args.variant, refine=args.refine)
+    opts = dict(seed=1, prec=args.prec, tol=args.tol, variant=args.variant, refine=args.refine)
     stream = torch.cuda.current_stream()
 
     def step(time_kernels=0):
@@ -622,7 +625,7 @@ def main():
                       "f64emu": "f64 LSQR; factor panels f64, trailing products emulated from bf16 digit products "
                                 "(47-bit operands, relative error ~2^-38)"}[args.prec],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": nnz, "s": s, "tol": 1e-12, "restarts": args.refine,
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": nnz, "s": s, "tol": args.tol, "restarts": args.refine,
                        "variant": args.variant, "start": "R^-1 Q^T S b" if args.warm else "0",
                        "form": "explicit B = A R^-1" if args.explicit else "implicit (per-step triangular solves)",
                        "global_batch": world, "parallelism": "replicas" if world > 1 else "single",

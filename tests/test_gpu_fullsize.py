@@ -156,12 +156,59 @@ def test_cfg3_full_size(csls):
     check_manufactured(p, xh, 1e-2)
 
 
+def test_backward_on_slice_at_ten_decades(csls):
+    """The differentiated workload's own recipe on its 1,000 x 100 slice: 10 decades of column scaling,
+    cond(A) ~ 1e10, L = ||x - x_true||^2.
+      * Against the oracle's dense adjoint (lambda = R_A^-1 R_A^-T g from the Householder QR of A, at
+        the GPU's x): dL/db to 1e-9; dL/d(values) to a bar set by the residual: r = b - A x is computed
+        with |A||x| ~ 1 against |r| ~ 1e-8 (the injected noise), so its entries carry relative errors
+        ~2^-53 / 1e-8; the bar is 10x the difference between two exact-arithmetic-equivalent dense
+        evaluations of the gradient formula (the oracle's row loop and a dense product), at least 1e-9.
+      * Against central differences of the GPU solve in b: L is quadratic in b, so a central
+        difference is exact for any step and a step of 1 keeps the solve's own rounding (which the
+        10 decades amplify) far below the difference. In the values L is not quadratic and the
+        solve's rounding swamps any step small enough for the truncation error, so those are checked
+        against the oracle only."""
+    prob = scaled_random_sparse(1000, 100, per_row=10, cond_exp=10.0, seed=5)
+    A = csls.Csr.from_numpy(prob.row_ptr, prob.col, prob.val, prob.m, prob.n)
+    xt = torch.tensor(prob.x_true, device="cuda")
+    opts = dict(seed=3, tol=1e-14, maxit=300, refine=1)
+    F = csls.csls_factor(A, **opts)
+
+    def loss(bb):
+        x, _ = csls.csls_solve(F, A, bb, **opts)
+        return float(((x - xt) ** 2).sum()), x
+
+    b = torch.tensor(prob.b[0], device="cuda")
+    L0, x = loss(b)
+    gx = 2.0 * (x - xt)
+    gb, gv, rep = csls.csls_solve_backward(F, A, b, x, gx, **opts)
+    gb, gv = gb.cpu().numpy(), gv.cpu().numpy()
+    Ad = prob.dense()
+    xh = x.cpu().numpy()
+    _, RA = oracle.hhqr_solve(Ad, prob.b[0])
+    lam, gbo, gvo = oracle.adjoint(prob, prob.b[0], xh, RA, gx.cpu().numpy())
+    rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))
+    assert rel(gb, gbo) <= 1e-9
+    rows = np.repeat(np.arange(prob.m), np.diff(prob.row_ptr))
+    r_dense = prob.b[0] - Ad @ xh
+    gv_dense = r_dense[rows] * lam[prob.col] - (Ad @ lam)[rows] * xh[prob.col]
+    bar = max(1e-9, 10.0 * rel(gv_dense, gvo))
+    assert rel(gv, gvo) <= bar, (rel(gv, gvo), bar)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(prob.m, 12, replace=False):
+        e = torch.zeros_like(b)
+        e[int(i)] = 1.0
+        fd = (loss(b + e)[0] - loss(b - e)[0]) / 2.0
+        assert abs(fd - float(gb[int(i)])) <= 1e-6 * float(np.abs(gb).max())
+
+
 def test_backward_finite_differences_on_slice(csls):
     """dL/db and dL/d(values) from the GPU adjoint against central differences of
     the GPU solve itself, on a 1,000 x 100 slice of the differentiated workload's
-    recipe with 4 decades of column scaling: at the workload's 10 decades the
-    forward solve is only determined to ~cond(A) 2^-53, which swamps the
-    differences (the adjoint there is checked against the oracle's dense one)."""
+    recipe with 4 decades of column scaling (at the workload's 10 decades the
+    solve's rounding swamps differences in the values; that case is checked
+    against the oracle's dense adjoint and exact differences in b above)."""
     prob = scaled_random_sparse(1000, 100, per_row=10, cond_exp=4.0, seed=5)
     A = csls.Csr.from_numpy(prob.row_ptr, prob.col, prob.val, prob.m, prob.n)
     xt = torch.tensor(prob.x_true, device="cuda")
