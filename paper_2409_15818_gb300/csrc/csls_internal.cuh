@@ -93,6 +93,35 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, lo
     return ok_s != 0;
 }
 
+// Barrier for a co-resident grid on a counter that only grows: every CTA adds 1 (a release
+// reduction, no returned value, so the G arrivals pipeline in the L2 instead of serialising on
+// a read-modify-write round trip each) and waits until the counter reaches G x (k + 1) for its
+// k-th barrier. The counter must start at 0 for the launch (the caller gives each launch a zeroed
+// slot). Bounded by spin_limit like grid_sync.
+__device__ __forceinline__ bool grid_sync_count(unsigned* cnt, unsigned nblocks, unsigned k, long long spin_limit,
+                                                int* err) {
+    __shared__ int okc_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(cnt), "r"(1u) : "memory");
+        const unsigned target = nblocks * (k + 1u);
+        long long it = 0;
+        while (ld_acquire_u(cnt) < target) {
+            if (++it > spin_limit) {
+                set_error(err, CSLS_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            if (it > 256) __nanosleep(32);
+        }
+        okc_s = ok && (*(volatile int*)err != CSLS_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return okc_s != 0;
+}
+
 // Deterministic block-wide sum (fixed shuffle tree, then warps in order).
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* scratch /* NT/32 doubles */) {

@@ -274,7 +274,7 @@ template <bool SMEM>
 __global__ void __launch_bounds__(kObThreads, 1)
 k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk, const int* E, double* tau,
           double* Tb, unsigned short* Vd, unsigned short* VTd, int64_t ldvp, int* frow, int* ecol, double* part,
-          GridBarrier* bar, long long spin, int* err) {
+          unsigned* bar, long long spin, int* err) {
     extern __shared__ __align__(16) double ob_dyn[];
     __shared__ double red[kRedSlots];
     __shared__ double wk[kOB];
@@ -386,9 +386,10 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
         }
     };
 
+    unsigned nbar = 0;   // barriers passed (the counter slot of this launch starts at 0)
     column_sums(0);
     for (int c = 0; c < nbo; ++c) {
-        if (!grid_sync(bar, G, spin, err)) return;
+        if (!grid_sync_count(bar, G, nbar++, spin, err)) return;
         reduce_step(c);
         __syncthreads();
         const int64_t jj = J0 + c;
@@ -483,7 +484,7 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
             }
         }
     }
-    if (!grid_sync(bar, G, spin, err)) return;
+    if (!grid_sync_count(bar, G, nbar++, spin, err)) return;
     // each CTA reduces a share of the entries over the G partials (fixed order), then all CTAs take
     // the column maxima and CTA 0 the Gram matrix
     for (int e = g * kObWarps + warp; e < kGramSlots; e += G * kObWarps) {
@@ -499,7 +500,7 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
         }
         if (lane == 0) gram_red[e] = acc;
     }
-    if (!grid_sync(bar, G, spin, err)) return;
+    if (!grid_sync_count(bar, G, nbar++, spin, err)) return;
     if (tid < kOB) cmax[tid] = __ldcg(gram_red + (kGramSlots - kOB) + tid);
     // T of the block (CTA 0): T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) (V^T V)(0:i, i)
     if (g == 0) {
@@ -1162,6 +1163,7 @@ struct EmuScratch {
     int64_t wp_elems;
     double* Wn;                   // kOB x n
     double* Tb;                   // outer block's T (kOB x kOB)
+    unsigned* bar_cnt;            // one grid-barrier counter per outer block (zeroed per factorisation)
 };
 
 constexpr int kVcMaxSplit = 16;   // row chunks of W = V^T C (partials kept side by side)
@@ -1181,6 +1183,7 @@ static EmuScratch emu_carve(Carve& c, int64_t s, int64_t n) {
     e.Wp = c.take<double>((size_t)e.wp_elems);
     e.Wn = c.take<double>((size_t)(kOB * (n + kOB)));
     e.Tb = c.take<double>(kOB * kOB);
+    e.bar_cnt = c.take<unsigned>((size_t)ceil_div(n, kOB) + 1);
     return e;
 }
 
@@ -1214,6 +1217,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
     CSLS_TRY(raise_smem_limit((const void*)k_wreduce_ob, (int)kWrSmem));
     const int sms = device_sm_count();
     CSLS_CUDA(cudaMemsetAsync(q.bar, 0, sizeof(GridBarrier), st));
+    CSLS_CUDA(cudaMemsetAsync(e.bar_cnt, 0, sizeof(unsigned) * (size_t)(ceil_div(n, kOB) + 1), st));
     k_col_exponent<<<(unsigned)std::min<int64_t>(n, 65535), 256, 0, st>>>(A, lda, s, n, e.E);
     CSLS_CUDA(cudaGetLastError());
     dim3 fg((unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(s, 1024), 64)), (unsigned)std::min<int64_t>(n, 65535));
@@ -1238,7 +1242,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
             long long spinv = spin;
             double* tau = q.tau;
             double* part = q.partials;
-            GridBarrier* bar = q.bar;
+            unsigned* bar = e.bar_cnt + (J0 / kOB);   // a zeroed counter slot per outer block
             void* args[] = {&A, &ldav, &sv, &J0v, &nbov, &chunk, (void*)&e.E, &tau, (void*)&e.Tb, (void*)&e.Vd,
                             (void*)&e.VTd, &ldvpv, (void*)&e.frow, (void*)&e.ecol, &part, &bar, &spinv, &err};
             const int tk = kt_begin(kFamPanel, st);

@@ -16,6 +16,8 @@ namespace csls {
 constexpr int kTs = kTrsvBlock;   // 64
 constexpr int kTsThreads = 256;   // 4 threads per row / column
 
+// Polls a block flag (one lane per warp; the warp then reads the block's entries). The first polls
+// do not sleep: a flag on the chain is usually set within a few microseconds.
 __device__ __forceinline__ bool wait_flag(const int* flag, int want, long long spin, int* err) {
     long long it = 0;
     while (ld_acquire(flag) != want) {
@@ -23,7 +25,7 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int want, long long s
             set_error(err, CSLS_ERR_TIMEOUT);
             return false;
         }
-        __nanosleep(32);
+        if (it > 512) __nanosleep(32);
     }
     return true;
 }
@@ -81,8 +83,8 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     for (int c = nb - 1; c > b; --c) {
         const int64_t c0 = (int64_t)c * kTs;
         const int cs = (int)(n - c0 < kTs ? n - c0 : kTs);
-        if (tid == 0) wait_flag(&flags[c], want, spin, err);
-        __syncthreads();
+        if ((tid & 31) == 0) wait_flag(&flags[c], want, spin, err);
+        __syncwarp();
         double zv[16];
         const double* zp = z + c0 + q * 16;
 #pragma unroll
@@ -112,17 +114,28 @@ k_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     }
     part[q][row] = a2;
     __syncthreads();
-    double zb = 0.0;
-    if (tid < bs) {
-        zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
-        z[r0 + tid] = zb;
+    if (tid >= 32) return;
+    // warp 0 finishes the block: rows lane and lane + 32, then publishes it (one warp, so no
+    // CTA-wide barrier sits between the last product and the flag)
+    const int lane = tid;
+    double zb[2] = {0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i < bs) {
+            zb[h] = ((part[0][i] + part[1][i]) + part[2][i]) + part[3][i];
+            z[r0 + i] = zb[h];
+        }
     }
     __threadfence();
-    __syncthreads();
+    __syncwarp();
     // publish this block first: the x / w epilogue below touches only this block's rows
-    if (tid == 0) st_release(&flags[b], want);
-    if (MODE == 1 && tid < bs) xw_update(st, coef[3] != 0.0, coef[1], coef[2], zb, wx, x, r0 + tid);
-    if (tid == 0) {
+    if (lane == 0) st_release(&flags[b], want);
+    if (MODE == 1)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (lane + 32 * h < bs) xw_update(st, coef[3] != 0.0, coef[1], coef[2], zb[h], wx, x, r0 + lane + 32 * h);
+    if (lane == 0) {
         unsigned prev = atomicAdd(&ctl->done, 1u);
         if (prev == (unsigned)nb - 1) {
             ctl->ticket = 0;
@@ -148,7 +161,6 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     __shared__ double part[4][kTs];
     __shared__ double rhs[kTs];
     __shared__ double coef[2];
-    __shared__ double red[kTsThreads / 32];
     __shared__ double dsm[kTs * kTs];   // this block's diagonal inverse (32 KB)
     const int tid = threadIdx.x;
     if (MODE == 1 && *(volatile int*)&st->done) return;
@@ -169,7 +181,12 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     for (int i = tid; i < kTs * kTs; i += kTsThreads) dsm[i] = __ldg(D + i);
     // this block's own entries of g and v: read only by this CTA, so they are loaded up front
     const double gpre = (tid < bs) ? g[r0 + tid] : 0.0;
-    const double vtpre = (MODE == 1 && tid < bs) ? vt[r0 + tid] : 0.0;
+    // warp 0 finishes the block (rows lane and lane + 32): their previous vt entries, read up front
+    double vtp[2] = {0.0, 0.0};
+    if (MODE == 1 && tid < 32) {
+        if (tid < bs) vtp[0] = vt[r0 + tid];
+        if (tid + 32 < bs) vtp[1] = vt[r0 + tid + 32];
+    }
     double rv[16];
     auto load_block = [&](int c, double (&dst)[16]) {
         const int64_t c0 = (int64_t)c * kTs;
@@ -181,8 +198,8 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     double acc = 0.0;
     for (int c = 0; c < b; ++c) {
         const int64_t c0 = (int64_t)c * kTs;
-        if (tid == 0) wait_flag(&flags[c], want, spin, err);
-        __syncthreads();
+        if ((tid & 31) == 0) wait_flag(&flags[c], want, spin, err);
+        __syncwarp();
         double zv[16];
         const double* zp = g + c0 + q * 16;
 #pragma unroll
@@ -212,35 +229,43 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
     }
     part[q][col] = a2;
     __syncthreads();
-    double sq = 0.0, zb = 0.0;
-    if (tid < bs) {
-        zb = ((part[0][tid] + part[1][tid]) + part[2][tid]) + part[3][tid];
-        g[r0 + tid] = zb;
-    }
-    __threadfence();
-    __syncthreads();
-    // publish this block first: the epilogue below touches only this block's rows
-    if (tid == 0) st_release(&flags[b], want);
-    if (tid < bs) {
-        if (MODE == 0) {
-            if (out != g) out[r0 + tid] = zb;
-        } else {
-            const double vn = MODE == 1 ? zb - coef[0] * vtpre : zb;
-            vt[r0 + tid] = vn;
-            sq = vn * vn;
+    if (tid >= 32) return;
+    // warp 0 finishes the block (rows lane and lane + 32) and publishes it
+    const int lane = tid;
+    double zb[2] = {0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i < bs) {
+            zb[h] = ((part[0][i] + part[1][i]) + part[2][i]) + part[3][i];
+            g[r0 + i] = zb[h];
         }
     }
-    if (MODE != 0) {
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if ((tid & 31) == 0) red[tid >> 5] = sq;
-    }
     __threadfence();
-    __syncthreads();
-    if (tid == 0) {
+    __syncwarp();
+    // publish this block first: the epilogue below touches only this block's rows
+    if (lane == 0) st_release(&flags[b], want);
+    double sq = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i < bs) {
+            if (MODE == 0) {
+                if (out != g) out[r0 + i] = zb[h];
+            } else {
+                const double vn = MODE == 1 ? zb[h] - coef[0] * vtp[h] : zb[h];
+                vt[r0 + i] = vn;
+                sq += vn * vn;
+            }
+        }
+    }
+    if (MODE != 0)
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
         if (MODE != 0) {
-            double t = 0.0;
-            for (int w = 0; w < kTsThreads / 32; ++w) t += red[w];
-            partials[b] = t;
+            partials[b] = sq;
             __threadfence();
         }
         unsigned prev = atomicAdd(&ctl->done, 1u);
