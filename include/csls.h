@@ -53,6 +53,11 @@ typedef enum {
 /* Human-readable name of a status code (static storage, never NULL). */
 const char* csls_status_string(int status);
 
+/* After a call returned CSLS_ERR_CUDA: the CUDA runtime's name and message for the error and the
+ * library source location that saw it (per host thread; empty before any error; no paper
+ * counterpart, a diagnostic). The string lives until the thread's next failing call. */
+const char* csls_last_cuda_error(void);
+
 /* ---------------------------------------------------------------- types */
 enum { CSLS_VARIANT_QR = 0, CSLS_VARIANT_SVD = 1 };   /* Algorithm 1 / Algorithm 2 */
 /* Arithmetic of the sketch and its factorisation:

@@ -26,7 +26,10 @@ PREC = {"f64": 0, "f32": 1, "f64emu": 2}
 class CslsError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__("%s failed: %s" % (where, _lib().csls_status_string(status).decode()))
+        msg = "%s failed: %s" % (where, _lib().csls_status_string(status).decode())
+        if status == 8:   # CSLS_ERR_CUDA: the runtime's own message
+            msg += " [%s]" % _lib().csls_last_cuda_error().decode()
+        super().__init__(msg)
 
 
 class csls_csr(ctypes.Structure):
@@ -63,6 +66,7 @@ class csls_report(ctypes.Structure):
 
 EXPORTS = {
     "csls_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "csls_last_cuda_error": (ctypes.c_char_p, []),
     "csls_opts_default": (None, [ctypes.c_void_p]),
     "csls_sketch_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "csls_sketch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,

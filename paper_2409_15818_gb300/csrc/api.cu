@@ -369,6 +369,8 @@ using namespace csls;
 
 extern "C" {
 
+const char* csls_last_cuda_error(void) { return csls::last_cuda_error(); }
+
 const char* csls_status_string(int status) {
     switch (status) {
         case CSLS_OK: return "CSLS_OK";

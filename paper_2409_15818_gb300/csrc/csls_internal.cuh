@@ -13,10 +13,19 @@
         if (csls_rc_ != CSLS_OK) return csls_rc_;       \
     } while (0)
 
-#define CSLS_CUDA(expr)                                 \
-    do {                                                \
-        cudaError_t csls_ce_ = (expr);                  \
-        if (csls_ce_ != cudaSuccess) return CSLS_ERR_CUDA; \
+namespace csls {
+void note_cuda_error(cudaError_t e, const char* where);   // kept per host thread for csls_last_cuda_error
+const char* last_cuda_error();
+}
+#define CSLS_STR2_(x) #x
+#define CSLS_STR_(x) CSLS_STR2_(x)
+#define CSLS_CUDA(expr)                                                            \
+    do {                                                                           \
+        cudaError_t csls_ce_ = (expr);                                             \
+        if (csls_ce_ != cudaSuccess) {                                             \
+            csls::note_cuda_error(csls_ce_, __FILE__ ":" CSLS_STR_(__LINE__));     \
+            return CSLS_ERR_CUDA;                                                  \
+        }                                                                          \
     } while (0)
 
 namespace csls {

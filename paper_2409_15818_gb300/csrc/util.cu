@@ -1,5 +1,6 @@
 // Scans, segmented sorts, CSR validation and the transposed copy of A.
 #include <climits>
+#include <cstdio>
 
 #include <vector>
 
@@ -10,6 +11,20 @@
 #include "csls_internal.cuh"
 
 namespace csls {
+
+namespace {
+thread_local char g_last_cuda_error[256] = "";
+}  // namespace
+
+void note_cuda_error(cudaError_t e, const char* where) {
+    const char* file = where;
+    for (const char* p = where; *p; ++p)
+        if (*p == '/') file = p + 1;
+    snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s (%s) at %s", cudaGetErrorName(e),
+             cudaGetErrorString(e), file);
+}
+
+const char* last_cuda_error() { return g_last_cuda_error; }
 
 namespace {
 constexpr int kMaxDev = 64;
