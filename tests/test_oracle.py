@@ -471,3 +471,25 @@ def test_threaded_qr_is_bit_identical():
     F4, t4 = oracle.householder_qr(M)
     oracle.set_threads(prev)
     assert np.array_equal(F1, F4) and np.array_equal(t1, t4)
+
+
+def test_restart_reaches_the_dense_solution():
+    """The implicit form's rounding floor moves with the sketch: on a 3x2-box RFM system (cond ~1e9)
+    the first solves of two sketches end ~1e-10 apart in the A-norm and as far from the dense
+    Householder solution; one LSQR restart from the solution found (the correction from
+    r = b - A x) brings both to the dense solution (the same point by an independent route)."""
+    p = poisson2d(3, 2, 150, 24, 24, R=2.0, seed=2)
+    Ad = p.dense()
+    b = p.b[0]
+    an = lambda x, r: np.linalg.norm(Ad @ (x - r)) / np.linalg.norm(Ad @ r)
+    first, restarted = [], []
+    for seed in (1, 2):
+        first.append(oracle.csqrp_lsqr(p, b, seed=seed)[1])
+        fac, x, info = oracle.csqrp_lsqr(p, b, seed=seed, refine=1)
+        assert info["iterations_refine"] > 0
+        restarted.append(x)
+    x_hh, _ = oracle.hhqr_solve(Ad, b)
+    assert an(first[0], first[1]) > 1e-11
+    assert an(restarted[0], restarted[1]) <= 1e-13
+    for x in restarted:
+        assert an(x, x_hh) <= 1e-13
