@@ -52,6 +52,9 @@ def parse():
                     help="start LSQR from the sketch-and-solve point R^-1 Q^T S b (Remark 3.1)")
     ap.add_argument("--variant", default="qr", choices=["qr", "svd"],
                     help="preconditioner: QR of the sketch (Algorithm 1) or truncated SVD (Algorithm 2)")
+    ap.add_argument("--backward", action="store_true",
+                    help="each step also runs the adjoint backward of L = ||x - x_true||^2 (dL/db and dL/d values; "
+                         "workloads with a known x_true)")
     ap.add_argument("--tol", type=float, default=1e-8,
                     help="LSQR stopping tolerance atol = btol (the tau of Section 4.1); with one restart the "
                          "A-norm accuracy is far below it (the first solve stops at its rounding floor anyway)")
@@ -70,22 +73,35 @@ def peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def read_ceiling_gbs():
-    """Streaming-read bandwidth of this GPU (a reduction over 1 GiB, best of 10): the ceiling of
-    a read-only kernel such as SpMV, which the copy figure (reads + writes) does not give."""
+def read_ceiling_gbs(csls):
+    """Streaming-read bandwidth of this GPU, the ceiling of a read-dominated kernel such as SpMV
+    (the copy figure counts reads + writes): the library's probe kernel reads 2 GiB once per launch
+    (integer checksum, so no FP64 pipe limit), swept over CTAs per SM and loads in flight per
+    thread; the best configuration's median of 5 launches."""
     import torch
-    a = torch.ones(1 << 27, dtype=torch.float64, device="cuda")
-    a.sum()
-    best = float("inf")
-    for _ in range(10):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        a.sum()
-        e1.record()
-        torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1))
+    nbytes = 2 << 30
+    a = torch.ones(nbytes // 8, dtype=torch.float64, device="cuda")
+    best, cfg = 0.0, None
+    sweep = {}
+    for ctas in (1, 2, 4):
+        for unroll in (1, 2, 4, 8):
+            csls.csls_read_probe(a, ctas, unroll)
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                csls.csls_read_probe(a, ctas, unroll)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            gbs = nbytes / (statistics.median(ts) * 1e-3) / 1e9
+            sweep["%dx%d" % (ctas, unroll)] = round(gbs, 1)
+            if gbs > best:
+                sms = torch.cuda.get_device_properties(0).multi_processor_count
+                best, cfg = gbs, {"ctas_per_sm": ctas, "loads_in_flight_per_thread": unroll,
+                                  "bytes_in_flight": sms * ctas * 512 * unroll * 16}
     del a
-    return (1 << 30) / (best * 1e-3) / 1e9
+    return best, cfg, sweep
 
 
 def bf16_sustained():
@@ -355,6 +371,11 @@ def main():
     b = torch.tensor(p.b[0] if p.nrhs == 1 else p.b, device="cuda")   # cfg4a: 64 right-hand sides
     opts = dict(seed=1, prec=args.prec, tol=args.tol, variant=args.variant, refine=args.refine)
     stream = torch.cuda.current_stream()
+    if args.backward:
+        assert getattr(p, "x_true", None) is not None and p.nrhs == 1 and not (args.explicit or args.warm), \
+            "--backward needs a single right-hand side with a known x_true (the column-scaled workloads)"
+        xt = torch.tensor(p.x_true, device="cuda")
+        bopts = dict(opts, tol=1e-12)
 
     def step(time_kernels=0):
         # time_kernels: the factor brackets each launch of its QR kernel families with CUDA
@@ -376,6 +397,12 @@ def main():
             return F, x, rep
         F = csls.csls_factor(A, time_kernels=time_kernels, **opts)
         x, rep = csls.csls_solve(F, A, b, raise_on_error=False, **opts)
+        if args.backward:
+            # adjoint of L = ||x - x_true||^2: CG on B^T B to 1e-12 (its own stopping rule)
+            gb, gv, brep = csls.csls_solve_backward(F, A, b, x, 2.0 * (x - xt), **bopts)
+            rep["ms_backward"] = brep["ms_solve"]
+            rep["backward_iterations"] = brep["iterations"]
+            rep["backward_status"] = brep["status"]
         return F, x, rep
 
     for _ in range(args.warmup):
@@ -388,7 +415,7 @@ def main():
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
-    qr_ms, solve_ms, sketch_ms, iters = [], [], [], []
+    qr_ms, solve_ms, sketch_ms, iters, bwd_ms = [], [], [], [], []
     kern_ms, kern_n, kern_flop = [0.0] * 3, [0] * 3, [0.0] * 3
     e0.record(stream)
     for _ in range(args.steps):
@@ -402,6 +429,8 @@ def main():
         sketch_ms.append(F.report["ms_sketch"])
         solve_ms.append(rep["ms_solve"])
         iters.append(rep["iterations"])
+        if args.backward:
+            bwd_ms.append(rep["ms_backward"])
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -463,7 +492,7 @@ def main():
     del graph
     hbm, bf16, src = peaks()
     bf16_sus = bf16_sustained()
-    read_gbs = read_ceiling_gbs()
+    read_gbs, read_cfg, read_sweep = read_ceiling_gbs(csls)
     pair_gbs = spmv_pair_bytes(m, n, nnz) / (pair_ms * 1e-3) / 1e9
 
     # triangular-solve pair (z = R^-1 v, then R^-T z), each call timed with events on the stream
@@ -539,6 +568,10 @@ def main():
         # which the timed steps above have already run
         csls.csls_rfm_assemble(p.dim, r_half, p.J, h_k.cuda(), h_c.cuda(), h_rows.cuda())
     d2h = h_x.numel() * 8
+    if args.backward:   # the gradients come back too
+        h_gb = torch.empty(m, dtype=torch.float64).pin_memory()
+        h_gv = torch.empty(nnz, dtype=torch.float64).pin_memory()
+        d2h += (m + nnz) * 8
     torch.cuda.synchronize()
     q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(1, min(args.steps, 2))
@@ -562,6 +595,10 @@ def main():
         else:
             F2 = csls.csls_factor(A2, **opts)
             x2, _ = csls.csls_solve(F2, A2, b2, raise_on_error=False, **opts)
+            if args.backward:
+                gb2, gv2, _ = csls.csls_solve_backward(F2, A2, b2, x2, 2.0 * (x2 - xt), **bopts)
+                h_gb.copy_(gb2, non_blocking=True)
+                h_gv.copy_(gv2, non_blocking=True)
         h_x.copy_(x2, non_blocking=True)
     q1.record(stream)
     torch.cuda.synchronize()
@@ -634,7 +671,15 @@ def main():
             "iterations_restart": int(rep.get("iterations_refine", 0)),
             "phase_ms": {"sketch": statistics.median(sketch_ms), "factor": statistics.median(qr_ms),
                          "solve": statistics.median(solve_ms),
-                         **({"form_b": rep.get("ms_form_b")} if args.explicit else {})},
+                         **({"form_b": rep.get("ms_form_b")} if args.explicit else {}),
+                         **({"backward": statistics.median(bwd_ms)} if args.backward else {})},
+            "backward": {"loss": "||x - x_true||^2", "outputs": "dL/db (m) and dL/d values of A (nnz)",
+                         "method": "lambda = R^-1 mu, (B^T B) mu = R^-T g by CG reusing the forward factor",
+                         "cg_tol": 1e-12, "iterations": int(rep["backward_iterations"]),
+                         "status": csls.STATUS_NAMES.get(rep["backward_status"], rep["backward_status"]),
+                         "forward_plus_backward_s": (statistics.median(sketch_ms) + statistics.median(qr_ms) +
+                                                     statistics.median(solve_ms) + statistics.median(bwd_ms)) / 1e3}
+            if args.backward else None,
             "roofline": roofline,
             "cond_est": rep.get("cond_est"),
             "accuracy": accuracy,
@@ -643,7 +688,10 @@ def main():
             "spmv_pair": {"bound": "hbm", "achieved": pair_gbs, "peak": hbm, "unit": "GB/s", "frac": pair_gbs / hbm,
                           "ms": pair_ms, "bytes": spmv_pair_bytes(m, n, nnz), "peak_source": src + " copy (read + write)",
                           "read_only_ceiling": read_gbs, "frac_of_read_ceiling": pair_gbs / read_gbs,
-                          "read_ceiling_source": "torch sum over 1 GiB of fp64 (streaming read), best of 10"},
+                          "read_ceiling_source": "csls_read_probe: 2 GiB read once, 16-byte evict-first loads, integer "
+                                                 "checksum; best of a sweep over CTAs per SM x loads in flight "
+                                                 "per thread (GB/s per configuration in read_ceiling_sweep)",
+                          "read_ceiling_config": read_cfg, "read_ceiling_sweep": read_sweep},
             "cpu_baseline": cpu,
             "plain_f64_beside": plain,
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -226,6 +226,20 @@ int csls_spmv(const csls_factor_t* factor, const csls_csr* A, int trans, const d
               csls_stream_t stream);
 int csls_apply_workspace(const csls_factor_t* factor, size_t* bytes);
 
+/* ---------------------------------------------------------------- measurement */
+/* Streaming-read probe (no paper counterpart): the HBM read ceiling that the
+ * read-dominated SpMV pair is compared with. Reads `count` 8-byte words at `buf`
+ * (device, 16-byte aligned, caller-owned) once, with ctas_per_sm CTAs of 512 threads
+ * per SM, each thread keeping `unroll` independent 16-byte evict-first loads in
+ * flight (bytes in flight = SMs x ctas_per_sm x 512 x unroll x 16), and folds them
+ * into 64-bit wrap-around integer sums: partials (device, SMs x ctas_per_sm words)
+ * receives one per CTA; their wrap-around sum is the sum of the words. Asynchronous
+ * on `stream`. Errors: CSLS_ERR_ARG for a NULL partials (or a NULL buf with
+ * count > 0), a misaligned buf, count < 0, ctas_per_sm outside 1..4, or unroll
+ * other than 1, 2, 4 or 8. */
+int csls_read_probe(const void* buf, int64_t count, int ctas_per_sm, int unroll, unsigned long long* partials,
+                    csls_stream_t stream);
+
 /* ---------------------------------------------------------------- solve */
 /* Algorithm 1 steps 4-6 (Algorithm 2 steps 4-6): LSQR (Paige and Saunders 1982)
  * on min || A M y - b || from y = 0, returning x = M y. nrhs right-hand sides

@@ -101,6 +101,8 @@ EXPORTS = {
     "csls_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p]),
     "csls_apply_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "csls_read_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "csls_solve_workspace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "csls_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
@@ -404,6 +406,18 @@ def csls_spmv(F, A, x, trans=False, stream=None, y=None):
     _check(_lib().csls_spmv(F.handle, ctypes.byref(a), int(bool(trans)), _ptr(x), _ptr(y), _stream(stream)),
            "csls_spmv")
     return y
+
+
+def csls_read_probe(buf, ctas_per_sm=2, unroll=8, stream=None, partials=None):
+    """Streaming read of a device buffer (a multiple of 8 bytes, 16-byte aligned) by the library's
+    probe kernel; returns the per-CTA 64-bit wrap-around sums (int64 tensor, reinterpreted)."""
+    count = buf.numel() * buf.element_size() // 8
+    if partials is None:
+        sms = torch.cuda.get_device_properties(buf.device).multi_processor_count
+        partials = torch.empty(sms * ctas_per_sm, dtype=torch.int64, device=buf.device)
+    _check(_lib().csls_read_probe(_ptr(buf), count, int(ctas_per_sm), int(unroll), _ptr(partials), _stream(stream)),
+           "csls_read_probe")
+    return partials
 
 
 def csls_solve(F, A, b, opts=None, x=None, stream=None, raise_on_error=True, **kw):

@@ -651,6 +651,14 @@ int csls_spmv(const csls_factor_t* F, const csls_csr* A, int trans, const double
     return CSLS_OK;
 }
 
+int csls_read_probe(const void* buf, int64_t count, int ctas_per_sm, int unroll, unsigned long long* partials,
+                    csls_stream_t stream) {
+    if ((!buf && count > 0) || !partials || count < 0 || ((uintptr_t)buf & 15) != 0 || ctas_per_sm < 1 || ctas_per_sm > 4 ||
+        (unroll != 1 && unroll != 2 && unroll != 4 && unroll != 8))
+        return CSLS_ERR_ARG;
+    return csls::launch_read_probe(buf, count, ctas_per_sm, unroll, partials, (cudaStream_t)stream);
+}
+
 int csls_solve_workspace(const csls_factor_t* F, int64_t nrhs, size_t* bytes) {
     if (!F || !bytes || nrhs <= 0) return CSLS_ERR_ARG;
     Carve c{nullptr, 0, 0, true};

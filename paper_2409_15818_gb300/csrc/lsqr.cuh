@@ -248,5 +248,8 @@ int launch_pgemv(const double* P, int64_t n, int64_t r, int mode, const double* 
 // mode 0: y = P^T g. mode 1: vt = P^T g - (beta/alpha) vt + alpha update + scalar step. mode 2: start.
 int launch_pgemv_t(const double* P, int64_t n, int64_t r, int mode, const double* g, double* vt, double* out,
                    LsqrState* st, double* partials, double* hist, cudaStream_t s);
+// streaming-read probe: 64-bit checksum of `count` 8-byte words, one partial per CTA
+int launch_read_probe(const void* buf, int64_t count, int ctas_per_sm, int unroll, unsigned long long* partials,
+                      cudaStream_t s);
 
 }  // namespace csls

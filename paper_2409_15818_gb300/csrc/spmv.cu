@@ -315,3 +315,65 @@ int launch_pgemv_t(const double* P, int64_t n, int64_t r, int mode, const double
 }
 
 }  // namespace csls
+
+// ------------------------------------------------------------------ streaming-read probe
+//
+// The HBM read ceiling that the SpMV pair (a read-dominated stream) is compared with. Each thread
+// keeps U independent 16-byte loads in flight (evict-first) and folds them into a 64-bit integer
+// checksum: an FP64 sum would itself be the limit on this part (two FP64 additions per 16 bytes
+// per thread need more than the FP64 pipe's two operations per clock per SM at HBM rate).
+namespace csls {
+
+template <int U>
+__global__ void __launch_bounds__(512) k_read_probe(const ulonglong2* __restrict__ p, int64_t n2,
+                                                    const unsigned long long* __restrict__ tail, int has_tail,
+                                                    unsigned long long* partials) {
+    unsigned long long a0 = 0, a1 = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (U - 1) * stride < n2; i += U * stride) {
+        ulonglong2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldcs(p + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a0 += v[u].x;
+            a1 += v[u].y;
+        }
+    }
+    for (; i < n2; i += stride) {
+        const ulonglong2 v = __ldcs(p + i);
+        a0 += v.x;
+        a1 += v.y;
+    }
+    unsigned long long a = a0 + a1;
+    if (has_tail && blockIdx.x == 0 && threadIdx.x == 0) a += *tail;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    __shared__ unsigned long long ws[16];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+int launch_read_probe(const void* buf, int64_t count, int ctas_per_sm, int unroll, unsigned long long* partials,
+                      cudaStream_t s) {
+    const unsigned grid = (unsigned)(device_sm_count() * ctas_per_sm);
+    const ulonglong2* p = (const ulonglong2*)buf;
+    const int64_t n2 = count / 2;
+    const unsigned long long* tail = (const unsigned long long*)buf + (count - 1);
+    const int has_tail = (int)(count & 1);
+    switch (unroll) {
+        case 1: k_read_probe<1><<<grid, 512, 0, s>>>(p, n2, tail, has_tail, partials); break;
+        case 2: k_read_probe<2><<<grid, 512, 0, s>>>(p, n2, tail, has_tail, partials); break;
+        case 4: k_read_probe<4><<<grid, 512, 0, s>>>(p, n2, tail, has_tail, partials); break;
+        default: k_read_probe<8><<<grid, 512, 0, s>>>(p, n2, tail, has_tail, partials); break;
+    }
+    CSLS_CUDA(cudaGetLastError());
+    return CSLS_OK;
+}
+
+}  // namespace csls

@@ -638,3 +638,26 @@ def test_rfm_assembly_argument_errors(csls):
     c = torch.tensor(p.c, device="cuda")
     with pytest.raises(csls.CslsError):
         csls.csls_rfm_assemble(2, [0.25, -1.0], p.J, k, c, rows)
+
+
+@pytest.mark.parametrize("count", [0, 1, 7, 1 << 20, (1 << 20) + 3])
+def test_read_probe_checksum(csls, count):
+    """The streaming-read probe touches every word exactly once: its per-CTA partials sum (mod 2^64)
+    to the wrap-around sum of the buffer's 64-bit words, for every launch shape it accepts."""
+    rng = np.random.default_rng(count)
+    words = rng.integers(0, 2 ** 63, size=count, dtype=np.int64).view(np.uint64)
+    expect = int(np.sum(words, dtype=np.uint64))
+    buf = torch.from_numpy(words.view(np.int64).copy()).cuda()
+    for ctas, unroll in ((1, 1), (2, 8), (4, 4), (3, 2)):
+        part = csls.csls_read_probe(buf, ctas, unroll).cpu().numpy().view(np.uint64)
+        assert int(np.sum(part, dtype=np.uint64)) == expect
+
+
+def test_read_probe_argument_errors(csls):
+    buf = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(csls.CslsError):
+        csls.csls_read_probe(buf, 5, 8)
+    with pytest.raises(csls.CslsError):
+        csls.csls_read_probe(buf, 2, 3)
+    with pytest.raises(csls.CslsError):   # 8-byte offset: not 16-byte aligned
+        csls.csls_read_probe(buf[1:], 2, 8)
