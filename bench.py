@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="csls", choices=["csls", "reference"])
     ap.add_argument("--prec", default="f64emu", choices=["f64", "f32", "f64emu"])
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 solve timed beside")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle's CPU sample (cpu_baseline null), for secondary configurations")
     ap.add_argument("--config", default="cfg2")
     ap.add_argument("--assemble", action="store_true",
                     help="end-to-end leg: ship the RFM geometry and features, assemble the CSR on the GPU")
@@ -182,7 +184,7 @@ def replica_problem(config, rank):
 # ncu DRAM traffic per launch of the dominant factor kernels (dram__bytes_read.sum + dram__bytes_write.sum),
 # from the captures summarised under profiles/; None until a capture of the current kernel exists.
 TRAFFIC = {}
-TRAFFIC_SOURCE = None
+TRAFFIC_SOURCE = {}
 
 
 def oracle_cache(p, config):
@@ -615,42 +617,44 @@ def main():
                          "k_update_f64 (C -= V W, DMMA)"],
                  "f32": ["k_panel (FP32 Householder panel)", "k_vtc_f32 (W = V^T C, FP32 FMA)",
                          "k_update_f32 (C -= V W, FP32 FMA)"]}[args.prec]
-    top = max((1, 2), key=lambda f: kern_ms[f])
-    top_s = kern_ms[top] * 1e-3
+    fp64_alu_peak = 152 * 2 * 2 * 2.07e9 / 1e12   # TFLOP/s: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
     fp64_peak = 1100.0   # GFLOP/s: DMMA m16n8k16 .f64 with full-mantissa operands (= cuBLAS DGEMM on this part)
-    fams = {fam_names[f].split(" ")[0]: {"ms_total": kern_ms[f], "launches": kern_n[f],
-                                        "share_of_factor": kern_ms[f] / max(sum(qr_ms), 1e-9)} for f in range(3)}
+    # per family: its bound, the work it is rated on and the peak of that unit
     if args.prec == "f64emu":
-        # 21 exact bf16 digit-pair products per binary64 product (6 digits, levels p + q <= 5): the
-        # algorithmic bf16 tensor work of the kernel, against the measured dense bf16 rate
-        pairs = 21
-        ach = pairs * kern_flop[top] / top_s / 1e12
-        peak = bf16_sus
-        traffic = TRAFFIC.get(fam_names[top].split(" ")[0])
-        roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
-                    "traffic_source": TRAFFIC_SOURCE if traffic else None,
-                    "peak_source": src + " bf16 sustained (kernel timed inside a multi-second step)",
-                    "fp64_equivalent_tflops": kern_flop[top] / top_s / 1e12, "launches": kern_n[top],
-                    "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
+        # the products: 21 exact bf16 digit-pair products per binary64 product (6 digits, levels
+        # p + q <= 5), against the measured dense bf16 rate; the panel: FP64 arithmetic on the ALU pipe
+        spec = [("alu", 1.0, fp64_alu_peak, "FP64 FMA pipe: 152 SMs x 2 FMA/clock x 2 flop x 2.07 GHz"),
+                ("tensor", 21.0, bf16_sus, src + " bf16 sustained (kernel timed inside a multi-second step)"),
+                ("tensor", 21.0, bf16_sus, src + " bf16 sustained (kernel timed inside a multi-second step)")]
     elif args.prec == "f64":
-        ach = kern_flop[top] / top_s / 1e12
-        roofline = {"bound": "tensor", "kernel": fam_names[top], "achieved": ach, "peak": fp64_peak / 1e3,
-                    "unit": "TFLOP/s", "frac": ach / (fp64_peak / 1e3), "traffic": None,
-                    "peak_source": "measured DMMA m16n8k16 f64 rate with full-mantissa operands (1.10 TFLOP/s, "
-                                   "= cuBLAS DGEMM); bf16 x nominal fp64/bf16 ratio would give %.2f"
-                                   % (bf16 * 1.25 / 2250), "launches": kern_n[top],
-                    "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
+        dm = "measured DMMA m16n8k16 f64 rate with full-mantissa operands (1.10 TFLOP/s, = cuBLAS DGEMM)"
+        spec = [("alu", 1.0, fp64_alu_peak, "FP64 FMA pipe: 152 SMs x 2 FMA/clock x 2 flop x 2.07 GHz"),
+                ("tensor", 1.0, fp64_peak / 1e3, dm), ("tensor", 1.0, fp64_peak / 1e3, dm)]
     else:
-        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA lanes x clock
-        ach = kern_flop[top] / top_s / 1e12
-        roofline = {"bound": "alu", "kernel": fam_names[top], "achieved": ach, "peak": alu_peak,
-                    "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "launches": kern_n[top],
-                    "avg_launch_ms": kern_ms[top] / max(kern_n[top], 1), "families": fams}
+        alu32 = 152 * 128 * 2 * 2.07e9 / 1e12
+        spec = [("alu", 1.0, alu32, "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")] * 3
+    fams = {}
+    for f in range(3):
+        bound, mult, pk, psrc = spec[f]
+        name = fam_names[f].split(" ")[0]
+        secs = kern_ms[f] * 1e-3
+        ach = mult * kern_flop[f] / secs / 1e12 if secs > 0 and kern_flop[f] > 0 else None
+        traffic = TRAFFIC.get(name)
+        fams[name] = {"kernel": fam_names[f], "bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                      "frac": ach / pk if ach else None, "peak_source": psrc, "ms_total": kern_ms[f],
+                      "launches": kern_n[f], "avg_launch_ms": kern_ms[f] / max(kern_n[f], 1),
+                      "share_of_factor": kern_ms[f] / max(sum(qr_ms), 1e-9),
+                      "fp64_equivalent_tflops": kern_flop[f] / secs / 1e12 if secs > 0 else None,
+                      "traffic": traffic, "traffic_source": TRAFFIC_SOURCE.get(name) if traffic else None}
+    top = max(range(3), key=lambda f: kern_ms[f])
+    tname = fam_names[top].split(" ")[0]
+    roofline = {k: fams[tname][k] for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic",
+                                              "traffic_source", "peak_source", "launches", "avg_launch_ms",
+                                              "fp64_equivalent_tflops")}
+    roofline["families"] = fams
     roofline["qr_fp64_equivalent_tflops"] = qr_gflops / 1e3
     cpu = None
-    if rank == 0:
+    if rank == 0 and not args.no_cpu_baseline:
         total, sample, spent, threads = oracle_sample_seconds(p, s, int(statistics.median(iters)))
         cpu = {"value": total, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample}
     if rank == 0:

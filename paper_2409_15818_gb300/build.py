@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcsls.so")
-SOURCES = ["util.cu", "sketch.cu", "qr.cu", "qr_emu.cu", "trsv.cu", "spmv.cu", "svd.cu", "backward.cu", "block.cu", "batch.cu", "explicit.cu", "rfm.cu", "api.cu"]
+SOURCES = ["util.cu", "sketch.cu", "qr.cu", "qr_emu.cu", "trsv.cu", "trsv_cl.cu", "spmv.cu", "svd.cu", "backward.cu", "block.cu", "batch.cu", "explicit.cu", "rfm.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]

@@ -82,6 +82,8 @@ static int64_t sketch_rows(const csls_csr* A, const csls_opts* o) {
 struct FactorPersist {
     void* R;
     double* Dinv;
+    double* pack_up;
+    double* pack_lo;
     Transpose AT;
     double* P;
     double* sigma;
@@ -93,6 +95,13 @@ static FactorPersist persist_carve(Carve& c, const csls_csr* A, const csls_opts*
     const int esz = o->factor_prec == CSLS_PREC_F32 ? 4 : 8;   // R storage
     f.R = c.take<char>((size_t)(n * n * esz));
     f.Dinv = c.take<double>((size_t)(ceil_div(n, kTrsvBlock) * kTrsvBlock * kTrsvBlock));
+    if (o->factor_prec != CSLS_PREC_F32 && o->variant == CSLS_VARIANT_QR) {
+        f.pack_up = c.take<double>((size_t)trsv_pack_doubles(n));
+        f.pack_lo = c.take<double>((size_t)trsv_pack_doubles(n));
+    } else {
+        f.pack_up = nullptr;
+        f.pack_lo = nullptr;
+    }
     f.AT.row_ptr = c.take<int64_t>((size_t)n + 1);
     f.AT.col = c.take<int32_t>((size_t)std::max<int64_t>(A->nnz, 1));
     f.AT.val = c.take<double>((size_t)std::max<int64_t>(A->nnz, 1));
@@ -155,7 +164,7 @@ static FactorTemp temp_carve(Carve& c, const csls_csr* A, const csls_opts* o, in
     }
     t.z0 = c.take<double>((size_t)n);
     t.ctl = c.take<TrsvCtl>(1);
-    t.flags = c.take<int>((size_t)ceil_div(n, kTrsvBlock));
+    t.flags = c.take<int>((size_t)trsv_flag_ints(ceil_div(n, kTrsvBlock), n));
     return t;
 }
 
@@ -179,8 +188,8 @@ static SolveWs solve_carve(Carve& c, const csls_factor_t* F) {
     w.lo_part = c.take<double>((size_t)std::max<int64_t>(F->nblocks, (int64_t)device_sm_count() * 8) + 64);
     w.hist_cap = n + 4;
     w.hist = c.take<double>((size_t)(2 * (w.hist_cap + 2)));
-    w.flags_up = c.take<int>((size_t)F->nblocks);
-    w.flags_lo = c.take<int>((size_t)F->nblocks);
+    w.flags_up = c.take<int>((size_t)trsv_flag_ints(F->nblocks, n));
+    w.flags_lo = c.take<int>((size_t)trsv_flag_ints(F->nblocks, n));
     return w;
 }
 
@@ -193,7 +202,7 @@ struct ApplyWs {
 static ApplyWs apply_carve(Carve& c, const csls_factor_t* F) {
     ApplyWs w;
     w.ctl = c.take<TrsvCtl>(1);
-    w.flags = c.take<int>((size_t)F->nblocks);
+    w.flags = c.take<int>((size_t)trsv_flag_ints(F->nblocks, F->n));
     w.err = c.take<int>(1);
     return w;
 }
@@ -221,8 +230,8 @@ static int solve_one(const csls_factor_t* F, const csls_csr* A, const double* b,
     h.cs2 = -1.0;
     h.first = 1;
     CSLS_CUDA(cudaMemcpyAsync(w.st, &h, sizeof(LsqrState), cudaMemcpyHostToDevice, st));
-    CSLS_CUDA(cudaMemsetAsync(w.flags_up, 0, sizeof(int) * (size_t)F->nblocks, st));
-    CSLS_CUDA(cudaMemsetAsync(w.flags_lo, 0, sizeof(int) * (size_t)F->nblocks, st));
+    CSLS_CUDA(cudaMemsetAsync(w.flags_up, 0, sizeof(int) * (size_t)trsv_flag_count(F->nblocks, F->n), st));
+    CSLS_CUDA(cudaMemsetAsync(w.flags_lo, 0, sizeof(int) * (size_t)trsv_flag_count(F->nblocks, F->n), st));
     const bool warm = o->warm_start != 0;
     if (!warm) CSLS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st));
     CSLS_CUDA(cudaMemsetAsync(w.wx, 0, sizeof(double) * (size_t)n, st));
@@ -234,7 +243,7 @@ static int solve_one(const csls_factor_t* F, const csls_csr* A, const double* b,
         CSLS_CUDA(cudaGetLastError());
     }
     const int spg = spmv_grid(A);
-    TrsvArgs ta{F->R, F->prec, F->Dinv, n, (int)F->nblocks};
+    TrsvArgs ta{F->R, F->prec, F->Dinv, n, (int)F->nblocks, F->pack_up, F->pack_lo};
     double* hist = w.hist;
     if (warm) {
         // ||b|| for the stopping rule, then the start below runs on r0 = b - A x (the correction
@@ -508,6 +517,10 @@ static int factor_impl(const csls_csr* A, const double* b, double* x0, const csl
                                        &launches));
         CSLS_TRY(qr_extract_r_f64((const double*)ft.SA, ft.ld, n, (double*)fp.R, ft.stats, st));
         CSLS_TRY(diag_block_inverses_f64((const double*)fp.R, n, fp.Dinv, st));
+        if (fp.pack_up) {
+            CSLS_TRY(trsv_build_packs((const double*)fp.R, n, fp.Dinv, fp.pack_up, fp.pack_lo, st));
+            launches += 2;
+        }
         if (b) CSLS_TRY(qr_extract_qtb_f64((const double*)ft.SA, ft.ld, n, ft.z0, st));
     } else {
         CSLS_TRY(qr_factor_f32((float*)ft.SA, ft.ld, s, ncols, ft.qr, ft.err, spin, st, &launches));
@@ -518,9 +531,9 @@ static int factor_impl(const csls_csr* A, const double* b, double* x0, const csl
     if (b) {
         // x0 = R^-1 z0: the minimiser of ||S (A x - b)|| (Remark 3.1's y0 = Q^T S b, x0 = R^-1 y0)
         TrsvArgs ta{fp.R, o->factor_prec == CSLS_PREC_F32 ? CSLS_PREC_F32 : CSLS_PREC_F64, fp.Dinv, n,
-                    (int)ceil_div(n, kTrsvBlock)};
+                    (int)ceil_div(n, kTrsvBlock), fp.pack_up, fp.pack_lo};
         CSLS_CUDA(cudaMemsetAsync(ft.ctl, 0, sizeof(TrsvCtl), st));
-        CSLS_CUDA(cudaMemsetAsync(ft.flags, 0, sizeof(int) * (size_t)ta.nb, st));
+        CSLS_CUDA(cudaMemsetAsync(ft.flags, 0, sizeof(int) * (size_t)trsv_flag_count(ta.nb, n), st));
         CSLS_TRY(launch_trsv_upper(ta, 0, ft.z0, x0, ft.flags, ft.ctl, nullptr, nullptr, nullptr, spin, ft.err, st));
         launches += 2;
     }
@@ -561,6 +574,7 @@ static int factor_impl(const csls_csr* A, const double* b, double* x0, const csl
     F->variant = o->variant;
     F->prec = o->factor_prec == CSLS_PREC_F32 ? CSLS_PREC_F32 : CSLS_PREC_F64;   // storage type of R
     F->R = fp.R; F->Dinv = fp.Dinv; F->P = fp.P; F->AT = fp.AT;
+    F->pack_up = fp.pack_up; F->pack_lo = fp.pack_lo;
     F->rdiag_min = stats[0]; F->rdiag_max = stats[1];
     F->nblocks = ceil_div(n, kTrsvBlock);
     F->a_col = A->col;
@@ -625,10 +639,10 @@ int csls_precond_apply(const csls_factor_t* F, int trans, const double* v, doubl
     Carve c{(char*)work, 0, work_bytes, false};
     ApplyWs w = apply_carve(c, F);
     CSLS_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(TrsvCtl), st));
-    CSLS_CUDA(cudaMemsetAsync(w.flags, 0, sizeof(int) * (size_t)F->nblocks, st));
+    CSLS_CUDA(cudaMemsetAsync(w.flags, 0, sizeof(int) * (size_t)trsv_flag_count(F->nblocks, F->n), st));
     CSLS_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     if (F->variant == CSLS_VARIANT_QR) {
-        TrsvArgs ta{F->R, F->prec, F->Dinv, F->n, (int)F->nblocks};
+        TrsvArgs ta{F->R, F->prec, F->Dinv, F->n, (int)F->nblocks, F->pack_up, F->pack_lo};
         if (!trans) {
             CSLS_TRY(launch_trsv_upper(ta, 0, v, z, w.flags, w.ctl, nullptr, nullptr, nullptr, 20000000LL, w.err, st));
         } else {

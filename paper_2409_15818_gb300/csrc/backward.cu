@@ -156,8 +156,8 @@ BackwardWs backward_ws_carve(Carve& c, int64_t m, int64_t n, int64_t nb) {
     w.lam = c.take<double>((size_t)n);
     w.w = c.take<double>((size_t)m);
     w.partials = c.take<double>((size_t)device_sm_count() * 8 + 64);
-    w.flags_up = c.take<int>((size_t)nb);
-    w.flags_lo = c.take<int>((size_t)nb);
+    w.flags_up = c.take<int>((size_t)trsv_flag_ints(nb, n));
+    w.flags_lo = c.take<int>((size_t)trsv_flag_ints(nb, n));
     w.ctl = c.take<TrsvCtl>(2);
     w.err = c.take<int>(1);
     return w;
@@ -168,10 +168,10 @@ int backward_run(const csls_factor_t* F, const csls_csr* A, const double* b, con
                  cudaStream_t st) {
     const int64_t n = F->n, m = F->m;
     if (F->variant != CSLS_VARIANT_QR) return CSLS_ERR_ARG;
-    TrsvArgs ta{F->R, F->prec, F->Dinv, n, (int)F->nblocks};
+    TrsvArgs ta{F->R, F->prec, F->Dinv, n, (int)F->nblocks, F->pack_up, F->pack_lo};
     const long long spin = o->spin_limit;
-    CSLS_CUDA(cudaMemsetAsync(w.flags_up, 0, sizeof(int) * (size_t)F->nblocks, st));
-    CSLS_CUDA(cudaMemsetAsync(w.flags_lo, 0, sizeof(int) * (size_t)F->nblocks, st));
+    CSLS_CUDA(cudaMemsetAsync(w.flags_up, 0, sizeof(int) * (size_t)trsv_flag_count(F->nblocks, F->n), st));
+    CSLS_CUDA(cudaMemsetAsync(w.flags_lo, 0, sizeof(int) * (size_t)trsv_flag_count(F->nblocks, F->n), st));
     CSLS_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(TrsvCtl) * 2, st));
     CSLS_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     CgState hc{};

@@ -268,6 +268,8 @@ struct csls_factor_s {
     int variant, prec;
     void* R;               // n x n, ld n (double or float)
     double* Dinv;          // ceil(n/64) blocks of 64 x 64
+    double* pack_up;       // operand packs of the cluster-chain triangular solves (binary64 R, QR)
+    double* pack_lo;
     double* P;             // n x r (SVD)
     csls::Transpose AT;
     double rdiag_min, rdiag_max;

@@ -327,7 +327,7 @@ static ExWs ex_carve(Carve& c, const csls_factor_t* F) {
     w.hist_cap = r + 4;
     w.hist = c.take<double>((size_t)(2 * (r + 6)));
     w.ctl = c.take<TrsvCtl>(1);
-    w.flags = c.take<int>((size_t)F->nblocks);
+    w.flags = c.take<int>((size_t)trsv_flag_ints(F->nblocks, F->n));
     return w;
 }
 
@@ -444,9 +444,9 @@ int csls_solve_explicit(const csls_factor_t* F, const double* B, int64_t ldb, co
     CSLS_CUDA(cudaGetLastError());
     // x = R^-1 y  or  P y
     if (F->variant == CSLS_VARIANT_QR) {
-        TrsvArgs ta{F->R, F->prec, F->Dinv, n, (int)F->nblocks};
+        TrsvArgs ta{F->R, F->prec, F->Dinv, n, (int)F->nblocks, F->pack_up, F->pack_lo};
         CSLS_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(TrsvCtl), st));
-        CSLS_CUDA(cudaMemsetAsync(w.flags, 0, sizeof(int) * (size_t)F->nblocks, st));
+        CSLS_CUDA(cudaMemsetAsync(w.flags, 0, sizeof(int) * (size_t)trsv_flag_count(F->nblocks, F->n), st));
         CSLS_TRY(launch_trsv_upper(ta, 0, w.y, x, w.flags, w.ctl, nullptr, nullptr, nullptr, o->spin_limit,
                                    &w.st->err, st));
     } else {

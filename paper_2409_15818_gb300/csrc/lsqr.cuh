@@ -221,7 +221,28 @@ struct TrsvArgs {
     const double* Dinv;
     int64_t n;
     int nb;                 // ceil(n / 64)
+    const double* pack_up = nullptr;   // per-step operand packs of the cluster-chain solves (binary64 R)
+    const double* pack_lo = nullptr;
 };
+
+// Synchronisation words of one solve direction, all zeroed before a solve's first launch: nb flag
+// words (the one-CTA-per-block kernel), then, 16-byte aligned, two arrays of n + 64 tagged 16-byte
+// words (the cluster-chain kernel: the chain's solutions for its workers, the workers' far sums).
+inline int64_t trsv_flag_ints(int64_t nb, int64_t n) { return ((nb + 3) & ~(int64_t)3) + 8 * (n + 64); }
+inline int64_t trsv_flag_count(int64_t nb, int64_t n) { return trsv_flag_ints(nb, n); }
+inline ulonglong2* trsv_tagged(int* flags, int64_t nb) {
+    return reinterpret_cast<ulonglong2*>(flags + ((nb + 3) & ~(int64_t)3));
+}
+// doubles of one direction's operand pack (ceil(n / 64) x 8 ranks x the per-step slot)
+int64_t trsv_pack_doubles(int64_t n);
+int trsv_build_packs(const double* R, int64_t n, const double* Dinv, double* pack_up, double* pack_lo,
+                     cudaStream_t s);
+// whether this device can keep the chain cluster and a worker cluster resident together
+bool trsv_cluster_usable();
+int launch_trsv_cl_upper(const TrsvArgs& a, int mode, const double* v, double* z, int* flags, TrsvCtl* ctl,
+                         LsqrState* st, double* wx, double* x, long long spin, int* err, cudaStream_t s);
+int launch_trsv_cl_lower(const TrsvArgs& a, int mode, double* g, double* vt, double* out, int* flags, TrsvCtl* ctl,
+                         LsqrState* st, double* hist, long long spin, int* err, cudaStream_t s);
 
 // mode 0: z = R^{-1} v. mode 1: LSQR step (v scaled by 1/alpha, x / wx epilogue).
 int launch_trsv_upper(const TrsvArgs& a, int mode, const double* v, double* z, int* flags, TrsvCtl* ctl,

@@ -1245,6 +1245,11 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
             unsigned* bar = e.bar_cnt + (J0 / kOB);   // a zeroed counter slot per outer block
             void* args[] = {&A, &ldav, &sv, &J0v, &nbov, &chunk, (void*)&e.E, &tau, (void*)&e.Tb, (void*)&e.Vd,
                             (void*)&e.VTd, &ldvpv, (void*)&e.frow, (void*)&e.ecol, &part, &bar, &spinv, &err};
+            // algorithmic FP64 work: Householder factorisation of the L x nbo block (2 nbo^2 (L - nbo / 3))
+            // and the strict upper Gram matrix of V for T (sum over b of 2 b (L - b))
+            const double fb = (double)nbo, fL = (double)L;
+            const double panel_flop = 2.0 * fb * fb * (fL - fb / 3.0) + fL * fb * (fb - 1.0) -
+                                      (fb - 1.0) * fb * (2.0 * fb - 1.0) / 3.0;
             const int tk = kt_begin(kFamPanel, st);
             if (in_smem)
                 CSLS_CUDA(cudaLaunchCooperativeKernel((const void*)k_obpanel<true>, dim3(G), dim3(kObThreads), args,
@@ -1252,7 +1257,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
             else
                 CSLS_CUDA(cudaLaunchCooperativeKernel((const void*)k_obpanel<false>, dim3(G), dim3(kObThreads), args,
                                                       0, st));
-            kt_end(tk, 0.0, st);
+            kt_end(tk, panel_flop, st);
             nl += 1;
         }
         const int64_t nprime = n - J0 - nbo;

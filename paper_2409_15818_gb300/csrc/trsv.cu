@@ -296,6 +296,8 @@ k_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, const double* __restri
 
 int launch_trsv_upper(const TrsvArgs& a, int mode, const double* v, double* z, int* flags, TrsvCtl* ctl,
                       LsqrState* st, double* wx, double* x, long long spin, int* err, cudaStream_t s) {
+    if (a.rprec == CSLS_PREC_F64 && a.pack_up && a.nb < 65536 && trsv_cluster_usable())
+        return launch_trsv_cl_upper(a, mode, v, z, flags, ctl, st, wx, x, spin, err, s);
     dim3 grid((unsigned)a.nb), block(kTsThreads);
     if (a.rprec == CSLS_PREC_F64) {
         const double* R = (const double*)a.R;
@@ -312,6 +314,8 @@ int launch_trsv_upper(const TrsvArgs& a, int mode, const double* v, double* z, i
 
 int launch_trsv_lower(const TrsvArgs& a, int mode, double* g, double* vt, double* out, int* flags, TrsvCtl* ctl,
                       LsqrState* st, double* partials, double* hist, long long spin, int* err, cudaStream_t s) {
+    if (a.rprec == CSLS_PREC_F64 && a.pack_lo && a.nb < 65536 && trsv_cluster_usable())
+        return launch_trsv_cl_lower(a, mode, g, vt, out, flags, ctl, st, hist, spin, err, s);
     dim3 grid((unsigned)a.nb), block(kTsThreads);
 #define CSLS_LOWER(TR, MD)                                                                                      \
     k_trsv_lower<TR, MD><<<grid, block, 0, s>>>((const TR*)a.R, a.n, a.nb, a.Dinv, g, vt, out, flags, ctl, st, \

@@ -661,3 +661,25 @@ def test_read_probe_argument_errors(csls):
         csls.csls_read_probe(buf, 2, 3)
     with pytest.raises(csls.CslsError):   # 8-byte offset: not 16-byte aligned
         csls.csls_read_probe(buf[1:], 2, 8)
+
+
+@pytest.mark.parametrize("n", [40, 150, 333, 2600, 9700])
+@pytest.mark.parametrize("prec", ["f64", "f64emu"])
+def test_precond_apply_chain_lengths(csls, n, prec):
+    """Both triangular solves with a binary64 R against the oracle's substitutions, over chain lengths
+    from one 64-row block to more blocks than an SM count (workers that start only after earlier
+    ones finish), with ragged last blocks; repeated launches give identical bits."""
+    rng = np.random.default_rng(n)
+    m = 3 * n + 17
+    A = random_sparse(m, n, 8, rng, scale_exp=3.0)
+    Ad = dev(csls, A)
+    F = csls.csls_factor(Ad, seed=5, prec=prec)
+    R = F.R().cpu().numpy()
+    v = rng.standard_normal(n)
+    vt = torch.tensor(v, device="cuda")
+    z = csls.csls_precond_apply(F, vt)
+    zt = csls.csls_precond_apply(F, vt, trans=True)
+    assert _rel(z.cpu().numpy(), oracle.trsv_upper(R, v)) < 1e-12
+    assert _rel(zt.cpu().numpy(), oracle.trsv_upper_trans(R, v)) < 1e-12
+    assert torch.equal(csls.csls_precond_apply(F, vt), z)
+    assert torch.equal(csls.csls_precond_apply(F, vt, trans=True), zt)
