@@ -181,10 +181,17 @@ def replica_problem(config, rank):
     return config_problem(config)
 
 
-# ncu DRAM traffic per launch of the dominant factor kernels (dram__bytes_read.sum + dram__bytes_write.sum),
-# from the captures summarised under profiles/; None until a capture of the current kernel exists.
-TRAFFIC = {}
-TRAFFIC_SOURCE = {}
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per average launch of each factor family
+# on the 2D bench workload: the per-unit bytes of one capture on the 6x6-box profiling workload (launch 41,
+# outer block 40: L = 26,240 rows, n' = 4,576 trailing columns) times the units of an average bench launch
+# (2.869e6 panel elements; 3.006e8 trailing-product elements). Traffic grows in proportion to these units:
+# the products stream C once (vtc) or twice (update), the panel reads its block once.
+TRAFFIC = {"k_obpanel": 12.27 * 2.869e6, "k_emu_vtc_tc": 8.196 * 3.006e8, "k_emu_update_tc": 15.871 * 3.006e8}
+_TSRC = ("profiles/%s_rfm6x6.md (ncu --set full, launch 41 of the 6x6-box workload): %.3f B per %s, scaled to an "
+         "average launch of the 2D bench workload")
+TRAFFIC_SOURCE = {"k_obpanel": _TSRC % ("obpanel", 12.27, "panel element (L x 64)"),
+                  "k_emu_vtc_tc": _TSRC % ("emu_vtc_tc", 8.196, "trailing element (L x n'; algorithmic 8)"),
+                  "k_emu_update_tc": _TSRC % ("emu_update_tc", 15.871, "trailing element (L x n'; algorithmic 16)")}
 
 
 def oracle_cache(p, config):
@@ -639,7 +646,7 @@ def main():
         name = fam_names[f].split(" ")[0]
         secs = kern_ms[f] * 1e-3
         ach = mult * kern_flop[f] / secs / 1e12 if secs > 0 and kern_flop[f] > 0 else None
-        traffic = TRAFFIC.get(name)
+        traffic = TRAFFIC.get(name) if (args.config == "cfg2" and args.prec == "f64emu") else None
         fams[name] = {"kernel": fam_names[f], "bound": bound, "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                       "frac": ach / pk if ach else None, "peak_source": psrc, "ms_total": kern_ms[f],
                       "launches": kern_n[f], "avg_launch_ms": kern_ms[f] / max(kern_n[f], 1),

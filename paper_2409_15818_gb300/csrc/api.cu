@@ -13,9 +13,10 @@ namespace csls {
 
 size_t backward_ws_bytes(int64_t m, int64_t n, int64_t nb);
 size_t block_ws_bytes(int64_t m, int64_t n, int64_t nb, int64_t nrhs);
-int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb, double* x,
-                int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep, cudaStream_t st,
-                int64_t* launches);
+size_t block_refine_bytes(int64_t m, int64_t n, int64_t nrhs);
+int block_solve_refined(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb,
+                        double* x, int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep,
+                        cudaStream_t st, int64_t* launches);
 constexpr int64_t kBlockMax = 64;   // right-hand sides per block pass
 
 // ------------------------------------------------------------------ validation kernel
@@ -679,7 +680,8 @@ int csls_solve_workspace(const csls_factor_t* F, int64_t nrhs, size_t* bytes) {
     solve_carve(c, F);
     size_t need = c.off;
     if (nrhs > 1 && F->variant == CSLS_VARIANT_QR)
-        need = std::max(need, block_ws_bytes(F->m, F->n, F->nblocks, std::min(nrhs, kBlockMax)));
+        need = std::max(need, block_ws_bytes(F->m, F->n, F->nblocks, std::min(nrhs, kBlockMax)) +
+                                  block_refine_bytes(F->m, F->n, std::min(nrhs, kBlockMax)));
     *bytes = need;
     return CSLS_OK;
 }
@@ -705,7 +707,7 @@ int csls_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64
         for (int64_t k0 = 0; k0 < nrhs; k0 += kBlockMax) {
             const int64_t nk = std::min(kBlockMax, nrhs - k0);
             csls_report rk{};
-            int sk = block_solve(F, A, b + k0 * ldb, nk, ldb, x + k0 * ldx, ldx, o, work, work_bytes, &rk, st,
+            int sk = block_solve_refined(F, A, b + k0 * ldb, nk, ldb, x + k0 * ldx, ldx, o, work, work_bytes, &rk, st,
                                  &launches);
             if (k0 == 0 && rep) *rep = rk;
             max_it = std::max<int64_t>(max_it, rk.iterations);

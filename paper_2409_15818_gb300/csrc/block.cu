@@ -429,6 +429,23 @@ size_t block_ws_bytes(int64_t m, int64_t n, int64_t nb, int64_t nrhs) {
     return c.off;
 }
 
+// scratch of a block restart, after the block solve's own workspace: the residuals (m x nrhs) and the
+// corrections (n x nrhs)
+size_t block_refine_bytes(int64_t m, int64_t n, int64_t nrhs) {
+    Carve c{nullptr, 0, 0, true};
+    c.take<double>((size_t)(m * nrhs));
+    c.take<double>((size_t)(n * nrhs));
+    return c.off;
+}
+
+__global__ void k_add_cols(double* x, int64_t ldx, const double* dx, int64_t n, int nrhs) {
+    const int64_t total = n * nrhs;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / n, i = e - k * n;
+        x[i + k * ldx] += dx[e];
+    }
+}
+
 int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb, double* x,
                 int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep, cudaStream_t st,
                 int64_t* launches) {
@@ -552,6 +569,48 @@ int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int6
     }
     if (launches) *launches += nl;
     return status;
+}
+
+}  // namespace csls
+
+namespace csls {
+
+// Block LSQR with restarts (opts.refine): after the solve, each restart solves the block for the
+// correction from the residuals r_k = b_k - A x_k and adds it to x (the block form of the single
+// solve's restart). Reports the first solve's maximum iteration count plus the restarts' maxima.
+int block_solve_refined(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb,
+                        double* x, int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep,
+                        cudaStream_t st, int64_t* launches) {
+    int sk = block_solve(F, A, b, nrhs, ldb, x, ldx, o, work, bytes, rep, st, launches);
+    if (o->refine <= 0) return sk;
+    const int64_t m = F->m, n = F->n;
+    const size_t own = block_ws_bytes(m, n, F->nblocks, nrhs);
+    if (bytes < own + block_refine_bytes(m, n, nrhs)) return CSLS_ERR_WORKSPACE;
+    Carve c{(char*)work + own, 0, bytes - own, false};
+    double* res = c.take<double>((size_t)(m * nrhs));
+    double* dx = c.take<double>((size_t)(n * nrhs));
+    int64_t its_ref = 0;
+    for (int64_t p = 0; p < o->refine && (sk == CSLS_OK || sk == CSLS_ERR_NOT_CONVERGED); ++p) {
+        for (int64_t k = 0; k < nrhs; ++k) CSLS_TRY(launch_residual(A, x + k * ldx, b + k * ldb, res + k * m, st));
+        csls_report rr{};
+        sk = block_solve(F, A, res, nrhs, m, dx, n, o, work, own, &rr, st, launches);
+        const int sms = device_sm_count();
+        k_add_cols<<<(unsigned)std::min<int64_t>(ceil_div(n * nrhs, 256), (int64_t)sms * 8), 256, 0, st>>>(
+            x, ldx, dx, n, (int)nrhs);
+        CSLS_CUDA(cudaGetLastError());
+        if (launches) *launches += nrhs + 1;
+        its_ref += rr.iterations;
+        if (rep) {
+            rep->rnorm = rr.rnorm;
+            rep->arnorm = rr.arnorm;
+            rep->istop = rr.istop;
+        }
+    }
+    if (rep) {
+        rep->iterations += its_ref;
+        rep->iterations_refine = its_ref;
+    }
+    return sk;
 }
 
 }  // namespace csls

@@ -240,6 +240,25 @@ def test_multi_rhs_block_matches_single_and_oracle(csls):
     assert rep["iterations"] >= repk["iterations"]
 
 
+def test_multi_rhs_block_restart_reaches_dense_solution(csls):
+    """Block LSQR with one restart (tol 1e-8, the bench's rule): every column within 1e-10 of the dense
+    Householder solution in the A-norm, and of the restarted single-right-hand-side solve; the report
+    counts the restart's iterations."""
+    modes = tuple((a, c) for a in range(1, 6) for c in range(1, 5))[:11]
+    p = poisson2d(3, 2, 37, 11, 9, R=1.5, seed=7, modes=modes)
+    A = dev(csls, p)
+    F = csls.csls_factor(A, seed=3)
+    B = torch.tensor(p.b, device="cuda")
+    X, rep = csls.csls_solve(F, A, B, tol=1e-8, refine=1)
+    assert rep["status"] == 0 and rep["iterations_refine"] > 0
+    Ad = p.dense()
+    for k in (0, 5, 10):
+        x_hh, _ = oracle.hhqr_solve(Ad, p.b[k])
+        assert _anorm_rel(Ad, X[k].cpu().numpy(), x_hh) <= 1e-10
+        xk, _ = csls.csls_solve(F, A, B[k], tol=1e-8, refine=1)
+        assert _anorm_rel(Ad, X[k].cpu().numpy(), xk.cpu().numpy()) <= 1e-10
+
+
 def test_multi_rhs_fixed_iterations_track_single(csls):
     rng = np.random.default_rng(27)
     A = random_sparse(3000, 150, 10, rng, scale_exp=3.0)
