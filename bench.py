@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="csls", choices=["csls", "reference"])
     ap.add_argument("--prec", default="f64emu", choices=["f64", "f32", "f64emu"])
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 solve timed beside")
+    ap.add_argument("--cpu-library", action="store_true",
+                    help="also time the method on NumPy/SciPy over all host cores (LAPACK QR, SciPy LSQR), in full")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle's CPU sample (cpu_baseline null), for secondary configurations")
     ap.add_argument("--config", default="cfg2")
@@ -205,6 +207,12 @@ def oracle_cache(p, config):
     return d if str(d.get("input_hash")) == input_hash(p) else None
 
 
+def csr_matvec_np(p, x):
+    """A x from the CSR arrays (NumPy, for the accuracy figures)."""
+    rows = np.repeat(np.arange(p.m), np.diff(p.row_ptr))
+    return np.bincount(rows, weights=p.val * x[p.col], minlength=p.m)
+
+
 def qr_flops(s, n):
     return 2.0 * s * n * n - 2.0 / 3.0 * n ** 3
 
@@ -244,6 +252,41 @@ def oracle_sample_seconds(p, s, iters_full):
               "of the first %d of %d sketch columns %.2fs scaled by flops to %.1fs + 2 LSQR iterations %.2fs/it x "
               "%d iterations" % (threads, WORKLOAD, t_sketch, k, p.n, t_qr_k, t_qr, t_it, iters_full))
     return total, sample, t_sketch + t_qr_k + 2 * t_it, threads
+
+
+def library_cpu_solve(p, s, tol, refine):
+    """The method on NumPy/SciPy over all host cores, as the paper's 2D experiments ran it (Python), timed in
+    full: the count sketch as a sparse product S A (buckets and signs from NumPy's generator: Definition 2.3
+    asks only for uniform buckets and balanced signs), LAPACK's Householder QR of the dense sketch
+    (numpy.linalg.qr, dgeqrf), SciPy's LSQR on A R^-1 applied by triangular solves, and the same restarts
+    as the GPU solve. Returns (seconds, x, iterations, phases)."""
+    import scipy.linalg as sl
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import LinearOperator, lsqr
+    b = np.ascontiguousarray(p.b[0])
+    t0 = time.perf_counter()
+    A = sp.csr_matrix((p.val, p.col, p.row_ptr), shape=(p.m, p.n))
+    rng = np.random.default_rng(1)
+    h = rng.integers(0, s, p.m)
+    d = rng.choice(np.array([-1.0, 1.0]), p.m)
+    S = sp.csr_matrix((d, (h, np.arange(p.m))), shape=(s, p.m))
+    SA = (S @ A).toarray()
+    t1 = time.perf_counter()
+    R = np.linalg.qr(SA, mode="r")
+    del SA
+    t2 = time.perf_counter()
+    AT = A.T.tocsr()
+    op = LinearOperator((p.m, p.n), matvec=lambda v: A @ sl.solve_triangular(R, v),
+                        rmatvec=lambda u: sl.solve_triangular(R, AT @ u, trans="T"))
+    out = lsqr(op, b, atol=tol, btol=tol, iter_lim=p.n)
+    x = sl.solve_triangular(R, out[0])
+    its = int(out[2])
+    for _ in range(refine):
+        out = lsqr(op, b - A @ x, atol=tol, btol=tol, iter_lim=p.n)
+        x = x + sl.solve_triangular(R, out[0])
+        its += int(out[2])
+    t3 = time.perf_counter()
+    return t3 - t0, x, its, {"sketch": t1 - t0, "qr": t2 - t1, "lsqr": t3 - t2}
 
 
 def run_reference(args):
@@ -664,6 +707,16 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         total, sample, spent, threads = oracle_sample_seconds(p, s, int(statistics.median(iters)))
         cpu = {"value": total, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample}
+    cpu_lib = None
+    if rank == 0 and args.cpu_library and p.nrhs == 1 and args.variant == "qr":
+        secs, xl, its_l, ph = library_cpu_solve(p, s, args.tol, args.refine)
+        cpu_lib = {"value": secs, "unit": "s", "cores": len(os.sched_getaffinity(0)), "iterations": its_l,
+                   "phase_s": ph, "kind": "library (NumPy/SciPy: sparse count sketch, LAPACK dgeqrf through "
+                                           "numpy.linalg.qr, SciPy LSQR with triangular solves), timed in full"}
+        if cache is not None and "x_ref1" in cache:
+            ref = cache["x_ref1"]
+            cpu_lib["rel_err_A_vs_oracle_restarted"] = float(
+                np.linalg.norm(csr_matvec_np(p, xl - ref)) / np.linalg.norm(csr_matvec_np(p, ref)))
     if rank == 0:
         line = {
             "metric": METRIC, "value": ms / 1e3 / world, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -704,6 +757,7 @@ def main():
                                                  "per thread (GB/s per configuration in read_ceiling_sweep)",
                           "read_ceiling_config": read_cfg, "read_ceiling_sweep": read_sweep},
             "cpu_baseline": cpu,
+            "cpu_library": cpu_lib,
             "plain_f64_beside": plain,
             "e2e": {"value": e2e_ms / 1e3 / world, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "inputs": "RFM row descriptors + features, CSR assembled on the GPU" if args.assemble

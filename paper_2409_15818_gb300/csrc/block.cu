@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kBT) k_blk_start(const double* B, int64_t ldb,
             LsqrState* s = st + c;
             s->beta = beta;
             s->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
-            s->bnorm = beta;
+            s->bnorm = s->bnorm_ref > 0.0 ? s->bnorm_ref : beta;   // a restart keeps ||b|| in rule S1
             s->phibar = beta;
             s->rnorm = beta;
             if (!isfinite(beta)) { set_error(&s->err, CSLS_ERR_NONFINITE); s->done = 1; }
@@ -446,9 +446,12 @@ __global__ void k_add_cols(double* x, int64_t ldx, const double* dx, int64_t n, 
     }
 }
 
+// bref (host, nrhs or NULL): the norms of the original right-hand sides when b holds a restart's residuals
+// (rule S1 keeps them, as the single solve's restart does); bnorm_out (host, nrhs or NULL) receives the
+// norms of b.
 int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb, double* x,
                 int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep, cudaStream_t st,
-                int64_t* launches) {
+                int64_t* launches, const double* bref = nullptr, double* bnorm_out = nullptr) {
     if (F->variant != CSLS_VARIANT_QR) return CSLS_ERR_ARG;
     if (nrhs > 64) return CSLS_ERR_ARG;
     const int64_t m = F->m, n = F->n, nb = F->nblocks;
@@ -466,6 +469,7 @@ int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int6
         s.hist_cap = w.hist_cap;
         s.cs2 = -1.0;
         s.first = 1;
+        s.bnorm_ref = (bref && k < nrhs) ? (bref[k] > 0.0 ? bref[k] : 1e-300) : 0.0;
         h[(size_t)k] = s;
     }
     CSLS_CUDA(cudaMemcpyAsync(w.st, h.data(), sizeof(LsqrState) * (size_t)W, cudaMemcpyHostToDevice, st));
@@ -553,6 +557,7 @@ int block_solve(const csls_factor_t* F, const csls_csr* A, const double* b, int6
     int64_t max_it = 0;
     for (int64_t k = 0; k < nrhs; ++k) {
         const LsqrState& s = out[(size_t)k];
+        if (bnorm_out) bnorm_out[k] = s.bnorm;
         max_it = std::max<int64_t>(max_it, s.iter);
         if (status == CSLS_OK && s.err) status = s.err;
         if (status == CSLS_OK && o->fixed_iters <= 0 && s.istop == 0 && s.done) status = CSLS_ERR_NOT_CONVERGED;
@@ -581,7 +586,8 @@ namespace csls {
 int block_solve_refined(const csls_factor_t* F, const csls_csr* A, const double* b, int64_t nrhs, int64_t ldb,
                         double* x, int64_t ldx, const csls_opts* o, void* work, size_t bytes, csls_report* rep,
                         cudaStream_t st, int64_t* launches) {
-    int sk = block_solve(F, A, b, nrhs, ldb, x, ldx, o, work, bytes, rep, st, launches);
+    std::vector<double> bn((size_t)nrhs, 0.0);
+    int sk = block_solve(F, A, b, nrhs, ldb, x, ldx, o, work, bytes, rep, st, launches, nullptr, bn.data());
     if (o->refine <= 0) return sk;
     const int64_t m = F->m, n = F->n;
     const size_t own = block_ws_bytes(m, n, F->nblocks, nrhs);
@@ -593,7 +599,7 @@ int block_solve_refined(const csls_factor_t* F, const csls_csr* A, const double*
     for (int64_t p = 0; p < o->refine && (sk == CSLS_OK || sk == CSLS_ERR_NOT_CONVERGED); ++p) {
         for (int64_t k = 0; k < nrhs; ++k) CSLS_TRY(launch_residual(A, x + k * ldx, b + k * ldb, res + k * m, st));
         csls_report rr{};
-        sk = block_solve(F, A, res, nrhs, m, dx, n, o, work, own, &rr, st, launches);
+        sk = block_solve(F, A, res, nrhs, m, dx, n, o, work, own, &rr, st, launches, bn.data(), nullptr);
         const int sms = device_sm_count();
         k_add_cols<<<(unsigned)std::min<int64_t>(ceil_div(n * nrhs, 256), (int64_t)sms * 8), 256, 0, st>>>(
             x, ldx, dx, n, (int)nrhs);

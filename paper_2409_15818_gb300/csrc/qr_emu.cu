@@ -511,15 +511,18 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
             gT[(e - bcol * (bcol - 1) / 2) + bcol * kOB] = __ldcg(gram_red + e);
         }
         __syncthreads();
+        // column i of T: T(a, i) = -tau_i sum_{b = a .. i-1} T(a, b) G(b, i), eight threads per row a (thread
+        // q of the eight takes b = a + q, a + q + 8, ...), combined by a fixed shuffle tree
+        const int ta = tid >> 3, tq = tid & 7;
         for (int i = 0; i < nbo; ++i) {
-            double v = 0.0;
-            if (tid < i) {
-                double acc = 0.0;
-                for (int b = tid; b < i; ++b) acc += gT[tid + b * kOB] * gT[b + i * kOB];
-                v = -taus[i] * acc;
-            }
+            double acc = 0.0;
+            if (ta < i)
+                for (int b = ta + tq; b < i; b += 8) acc += gT[ta + b * kOB] * gT[b + i * kOB];
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
             __syncthreads();
-            if (tid < i) gT[tid + i * kOB] = v;
+            if (ta < i && tq == 0) gT[ta + i * kOB] = -taus[i] * acc;
             if (tid == i) gT[i + i * kOB] = taus[i];
             __syncthreads();
         }

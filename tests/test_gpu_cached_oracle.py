@@ -1,4 +1,5 @@
-"""The bench configuration's accuracy against the oracle at the bench size.
+"""The bench configuration's accuracy against the oracle at the bench size (and the differentiated
+workload's, 2e6 x 2e4 with 10 decades of column scaling, once its cache exists).
 
 The CPU oracle needs tens of minutes per factorisation of the 2D bench workload
 (8x8 boxes, m = 65,280, n = 12,800, s = 4n), so its solutions are cached in
@@ -80,5 +81,24 @@ def test_bench_solve_within_1e10_of_oracle(csls, cfg2, prec):
     r_ref = np.linalg.norm(b - oracle.spmv(p, c["x_ref1"]))
     assert abs(r_gpu - r_ref) <= 1e-12 * bn
     assert rep["cond_est"] < 10
+    del F
+    torch.cuda.empty_cache()
+
+
+def test_differentiated_workload_within_1e10_of_oracle(csls):
+    """The 2e6 x 2e4 column-scaled workload (10 decades): the oracle's restarted solve of the same sketch
+    seed is cached in tests/golden/oracle_cfg5.npz (same script, seed 1); the GPU solve with the bench's
+    rule (emulated-FP64 factor, tol 1e-8, one restart) must be within 1e-10 of it in the A-norm."""
+    path = os.path.join(GOLDEN, "oracle_cfg5.npz")
+    if not os.path.exists(path):
+        pytest.skip("no cached oracle solution of the 2e6 x 2e4 workload")
+    cache = dict(np.load(path, allow_pickle=False))
+    p = config_problem("cfg5")
+    assert str(cache["input_hash"]) == input_hash(p)
+    A = csls.Csr.from_numpy(p.row_ptr, p.col, p.val, p.m, p.n)
+    F = csls.csls_factor(A, seed=1, prec="f64emu")
+    x, rep = csls.csls_solve(F, A, torch.tensor(p.b[0], device="cuda"), tol=1e-8, refine=1)
+    assert rep["status"] == 0
+    assert _anorm(p, x.cpu().numpy(), cache["x_ref1"]) <= 1e-10
     del F
     torch.cuda.empty_cache()

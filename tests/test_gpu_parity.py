@@ -240,10 +240,11 @@ def test_multi_rhs_block_matches_single_and_oracle(csls):
     assert rep["iterations"] >= repk["iterations"]
 
 
-def test_multi_rhs_block_restart_reaches_dense_solution(csls):
-    """Block LSQR with one restart (tol 1e-8, the bench's rule): every column within 1e-10 of the dense
-    Householder solution in the A-norm, and of the restarted single-right-hand-side solve; the report
-    counts the restart's iterations."""
+def test_multi_rhs_block_restart_matches_oracle_restart(csls):
+    """Block LSQR with one restart (tol 1e-8, the bench's rule) against the oracle's restarted CSQRP-LSQR
+    of the same sketch, the dense solve and the restarted single-right-hand-side GPU solve. This RFM system
+    is far from consistent (||r|| / ||b|| ~ 1e-2), so at tol 1e-8 rule S2 leaves the oracle itself ~2e-10
+    from the dense solve: the bar is max(1e-10, twice that distance)."""
     modes = tuple((a, c) for a in range(1, 6) for c in range(1, 5))[:11]
     p = poisson2d(3, 2, 37, 11, 9, R=1.5, seed=7, modes=modes)
     A = dev(csls, p)
@@ -253,10 +254,14 @@ def test_multi_rhs_block_restart_reaches_dense_solution(csls):
     assert rep["status"] == 0 and rep["iterations_refine"] > 0
     Ad = p.dense()
     for k in (0, 5, 10):
+        _, xo, _ = oracle.csqrp_lsqr(p, p.b[k], seed=3, tol=1e-8, refine=1)
         x_hh, _ = oracle.hhqr_solve(Ad, p.b[k])
-        assert _anorm_rel(Ad, X[k].cpu().numpy(), x_hh) <= 1e-10
+        xg = X[k].cpu().numpy()
+        bar = max(1e-10, 2 * _anorm_rel(Ad, xo, x_hh))   # the problem's own spread at this tolerance
+        assert _anorm_rel(Ad, xg, xo) <= bar
+        assert _anorm_rel(Ad, xg, x_hh) <= bar
         xk, _ = csls.csls_solve(F, A, B[k], tol=1e-8, refine=1)
-        assert _anorm_rel(Ad, X[k].cpu().numpy(), xk.cpu().numpy()) <= 1e-10
+        assert _anorm_rel(Ad, xg, xk.cpu().numpy()) <= bar
 
 
 def test_multi_rhs_fixed_iterations_track_single(csls):
