@@ -184,8 +184,9 @@ int csls_sketch_noalloc(const csls_csr* A, int64_t s, uint64_t seed, int prec, v
  * diagonal; for the SVD variant also the one-sided Jacobi SVD R = U Sigma V^T
  * and P = V_r Sigma_r^{-1} with r = #{sigma_i > rcond sigma_1}. Also builds the
  * transposed CSR of A used for A^T u.
- * Two workspaces: `persist` holds the factor (R or P, block inverses, A^T) and
- * must outlive the handle; `temp` (the dense sketch and QR scratch) may be
+ * Two workspaces: `persist` holds the factor (R or P, block inverses, A^T, and for
+ * a binary64 QR factor the per-step operand packs of the triangular solves,
+ * 2 x ceil(n/64) x 160 KB) and must outlive the handle; `temp` (the dense sketch and QR scratch) may be
  * released once the call has returned. The handle itself is small host memory
  * owned by the library: release it with csls_factor_destroy (which frees no
  * device memory). rep may be NULL. */
@@ -248,6 +249,12 @@ int csls_read_probe(const void* buf, int64_t count, int ctas_per_sm, int unroll,
  * caller-owned device memory. A must be the matrix the factor was built from.
  * rep (host, may be NULL) is filled after a stream synchronisation; for nrhs > 1
  * it reports the first column and the maximum iteration count.
+ * With opts->refine > 0 each right-hand side (also in the block form) is
+ * restarted that many times: LSQR on the correction from r = b - A x, added to x.
+ * With a binary64 QR factor the triangular solves run as one cluster of 8 CTAs
+ * plus worker CTAs that must become resident as earlier ones finish: a GPU kept
+ * full by other work delays them, and a wait longer than 4 s ends the solve
+ * with CSLS_ERR_TIMEOUT.
  * Status: CSLS_ERR_NOT_CONVERGED if maxit was reached before S1/S2 held (x is
  * still the last iterate); CSLS_ERR_PRECOND_GUARD for a binary32 factor whose
  * cond estimate is >= guard_cond (x still written). */

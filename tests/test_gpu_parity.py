@@ -707,3 +707,37 @@ def test_precond_apply_chain_lengths(csls, n, prec):
     assert _rel(zt.cpu().numpy(), oracle.trsv_upper_trans(R, v)) < 1e-12
     assert torch.equal(csls.csls_precond_apply(F, vt), z)
     assert torch.equal(csls.csls_precond_apply(F, vt, trans=True), zt)
+
+
+@pytest.mark.parametrize("prec", ["f64emu", "f64", "f32"])
+def test_theorem_3_2_sweep_on_gpu(csls, prec):
+    """Theorem 3.2 on the GPU factors: with cond(A) swept over 12 decades by column scaling, cond(A R^-1)
+    (exact, from the dense B = A R^-1 with the GPU's R) stays below 10 and flat for the binary64 and
+    emulated factors. For every factor, the solve's estimate (the extreme singular values of the
+    Golub-Kahan bidiagonal it built) is a lower bound of that exact value, and the binary32 factor's guard
+    rejects it exactly when the estimate reaches 10."""
+    rng = np.random.default_rng(10)
+    base = random_sparse(2000, 50, 6, rng)
+    conds = []
+    guard = {v: k for k, v in csls.STATUS_NAMES.items()}["CSLS_ERR_PRECOND_GUARD"]
+    for p in (0, 4, 8, 12):
+        A = CSR(base.m, base.n, base.row_ptr, base.col, base.val * (10.0 ** (-p * np.arange(50) / 49))[base.col])
+        Ad = dev(csls, A)
+        F = csls.csls_factor(Ad, s=200, seed=3, prec=prec)
+        R = F.R().cpu().numpy().astype(np.float64)
+        B = np.linalg.solve(R.T, A.dense().T).T
+        c = float(np.linalg.cond(B))
+        conds.append(c)
+        b = torch.tensor(rng.standard_normal(base.m), device="cuda")
+        _, rep = csls.csls_solve(F, Ad, b, tol=1e-12, raise_on_error=False, prec=prec)
+        assert rep["cond_est"] <= c * (1 + 1e-3)
+        if prec == "f32":
+            assert rep["status"] == (guard if rep["cond_est"] >= 10 else 0)
+        else:
+            assert rep["status"] == 0
+        if p >= 8:
+            assert float(np.linalg.cond(A.dense())) > 1e6
+    if prec != "f32":
+        assert max(conds) < 10 and max(conds) / min(conds) < 1.5
+    else:
+        assert conds[0] < 10
