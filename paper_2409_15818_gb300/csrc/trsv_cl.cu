@@ -87,16 +87,8 @@ __device__ __forceinline__ void cl_st_f64(uint32_t a, double v) {
 __device__ __forceinline__ void cl_st_u32(uint32_t a, unsigned v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
-__device__ __forceinline__ bool cl_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, "
-        "0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(tc::smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
+// the pipeline barriers are all CTA-local (bulk-copy completions and this CTA's warps): acquire at CTA scope
+__device__ __forceinline__ bool cl_try_wait(uint64_t* bar, uint32_t parity) { return tc::mbar_try_wait(bar, parity); }
 // One 16-byte store of a value with its step tag into a CTA of the cluster: two 8-byte words, each
 // {half of the value's bits, tag}, each written whole.
 __device__ __forceinline__ void cl_send(uint32_t a, double v, unsigned tag) {
@@ -117,7 +109,8 @@ __device__ __forceinline__ bool cl_wait(uint64_t* bar, uint32_t parity, long lon
     for (long long it = 0;; ++it) {
         if (cl_try_wait(bar, parity)) return true;
         if (*(volatile int*)&sm.abort) return false;
-        if (it > spin || tc::global_ns() - t0 > kClWaitNs) {
+        // the wall clock is read every 256 polls only (its read is slow next to a poll)
+        if (it > spin || ((it & 255) == 255 && tc::global_ns() - t0 > kClWaitNs)) {
             set_error(err, CSLS_ERR_TIMEOUT);
             *(volatile int*)&sm.abort = 1;
             return false;
@@ -153,7 +146,7 @@ __device__ __forceinline__ bool poll_tagged(const ulonglong2* p, unsigned tag, u
         w = ld_tagged(p);
         if (tag_is(w, tag)) return true;
         if (sm && *(volatile int*)&sm->abort) return false;
-        if (++it > spin || tc::global_ns() - t0 > kClWaitNs) {
+        if (++it > spin || ((it & 255) == 255 && tc::global_ns() - t0 > kClWaitNs)) {
             set_error(err, CSLS_ERR_TIMEOUT);
             if (sm) *(volatile int*)&sm->abort = 1;
             return false;
@@ -181,7 +174,7 @@ __device__ __forceinline__ bool cl_recv4(const ulonglong2* p, unsigned tag, doub
         if (all) return true;
         if (*(volatile int*)&sm.abort) return false;
         if (it == 0) t0 = tc::global_ns();
-        if (it > spin || tc::global_ns() - t0 > kClWaitNs) {
+        if (it > spin || ((it & 255) == 255 && tc::global_ns() - t0 > kClWaitNs)) {
             set_error(err, CSLS_ERR_TIMEOUT);
             *(volatile int*)&sm.abort = 1;
             return false;
