@@ -85,15 +85,17 @@ def test_bench_solve_within_1e10_of_oracle(csls, cfg2, prec):
     torch.cuda.empty_cache()
 
 
-def test_differentiated_workload_within_1e10_of_oracle(csls):
-    """The 2e6 x 2e4 column-scaled workload (10 decades): the oracle's restarted solve of the same sketch
-    seed is cached in tests/golden/oracle_cfg5.npz (same script, seed 1); the GPU solve with the bench's
-    rule (emulated-FP64 factor, tol 1e-8, one restart) must be within 1e-10 of it in the A-norm."""
-    path = os.path.join(GOLDEN, "oracle_cfg5.npz")
+@pytest.mark.parametrize("config", ["cfg5", "cfg3"])
+def test_other_workloads_within_1e10_of_oracle(csls, config):
+    """The 2e6 x 2e4 column-scaled workload (10 decades) and the 3D RFM workload (4x4x4 boxes, n = 25,600):
+    the oracle's restarted solve of the same sketch seed is cached in tests/golden/oracle_<config>.npz (same
+    script, seed 1); the GPU solve with the bench's rule (emulated-FP64 factor, tol 1e-8, one restart) must
+    be within 1e-10 of it in the A-norm."""
+    path = os.path.join(GOLDEN, "oracle_%s.npz" % config)
     if not os.path.exists(path):
-        pytest.skip("no cached oracle solution of the 2e6 x 2e4 workload")
+        pytest.skip("no cached oracle solution of %s" % config)
     cache = dict(np.load(path, allow_pickle=False))
-    p = config_problem("cfg5")
+    p = config_problem(config)
     assert str(cache["input_hash"]) == input_hash(p)
     A = csls.Csr.from_numpy(p.row_ptr, p.col, p.val, p.m, p.n)
     F = csls.csls_factor(A, seed=1, prec="f64emu")
