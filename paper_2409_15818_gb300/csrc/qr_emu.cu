@@ -63,10 +63,32 @@ __device__ __forceinline__ void cut_digits(long long N, int (&d)[kDig]) {
     d[0] = hi >> 8;
 }
 
+// N = x 2^(47 - e) rounded to the nearest integer (ties to even), for |x| < 2^e, from the bit pattern
+// of x alone (integer instructions; FP64 ones are scarce on this part): x = m 2^e2 with the 53-bit
+// significand m, so N = m 2^-sh with sh = e - 47 - e2 >= 5 for normal x, and a right shift with
+// round-to-nearest-even gives it exactly (the same integer as rounding the exact product).
+__device__ __forceinline__ long long fix47(double x, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ev = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (ev != 0) m |= 1ull << 52;
+    const int sh = e - kNumBits - ((ev != 0 ? ev : 1) - 1075);
+    unsigned long long q;
+    if (sh <= 0) {
+        q = sh > -64 ? m << (-sh) : 0ull;
+    } else if (sh >= 64) {
+        q = 0ull;
+    } else {
+        q = m >> sh;
+        const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+    }
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
 // digits of x relative to scale 2^e (|x| < 2^e)
 __device__ __forceinline__ void digits_f64(double x, int e, int (&d)[kDig]) {
-    const long long N = __double2ll_rn(ldexp(x, kNumBits - e));
-    cut_digits(N, d);
+    cut_digits(fix47(x, e), d);
 }
 
 // digits of a fixed-point entry (|Cfix| < 2^62): N = round(Cfix / 2^(62 - 47))
@@ -257,44 +279,103 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
 // and the entry top_k = A(j, k). With beta = -sign(alpha) sqrt(alpha^2 + sigma), tau = (beta -
 // alpha) / beta and v = [1; x(1:) / (alpha - beta)], the product v^T A(j:s, k) = top_k + d_k /
 // (alpha - beta), so every CTA forms the reflector and updates its rows without a second
-// reduction. The same pass that computes the next column's sums also computes the Gram column
-// V(:, 0:c)^T v_c and the column maximum |v_c| (for T and the column-scaled digits), so the block
-// costs nbo + 1 grid barriers. Partials are summed in a fixed order (lane-strided, then a fixed
-// shuffle tree) by every CTA alike, so all CTAs hold identical bits and results are reproducible.
-// At the end CTA 0 forms T of the compact WY form (T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i)
-// V(:, 0:i)^T v_i), every CTA writes its rows of V / R back in binary64 and cuts them into the
-// row-scaled (Vd) and column-scaled (VTd) digit planes.
+// reduction. Partials are summed in a fixed order (lane-strided, then a fixed shuffle tree) by every
+// CTA alike, so all CTAs hold identical bits and results are reproducible.
+//
+// FP64 instructions are the scarce resource of this kernel (each FP64 warp instruction holds its
+// sub-partition's pipe for the same time whatever its active lanes), so the step is arranged to
+// issue few of them and to fill the pipe while the grid barrier settles:
+//  * the cross-CTA sums of a step cover only its live slots, packed onto full warps (8, 16 or 32
+//    lanes a slot by the number of live slots); thread 0 forms the reflector's scalars as soon as
+//    sigma is summed, with one reciprocal square root and one reciprocal;
+//  * dot products and the update spread over more lanes (and more warps) as the block's remaining
+//    columns shrink, so every sub-partition keeps work;
+//  * column c stays unscaled while the later columns are updated (the update uses w / (alpha -
+//    beta) on x), and becomes v in the same pass that forms the next column's sums;
+//  * each CTA arrives at the barrier of step c, then computes the Gram column V(:, 0:b)^T v_b and
+//    the maximum |v_b| of the finished column b = c - 1 over its rows, and only then waits.
+// The Gram matrix V^T V and the column maxima are reduced once at the end; CTA 0 forms T of the
+// compact WY form from them (right-looking: T(0:i, i) = -tau_i sum_b T(0:i, b) G(b, i), each
+// column of T added into the later ones as soon as it is final), every CTA writes its rows of V / R
+// back in binary64 and cuts them into the row-scaled (Vd) and column-scaled (VTd) digit planes
+// with integer operations.
 constexpr int kObThreads = 512;
 constexpr int kObWarps = kObThreads / 32;
 // reduced values of a step: sigma, alpha, d_k (64), top_k (64)
 constexpr int kRedSig = 0, kRedAlpha = 1, kRedD = 2, kRedTop = 2 + kOB, kRedSlots = 2 + 2 * kOB;
-constexpr size_t kObSmemCap = 180 * 1024;   // dynamic part (the static part is ~41 KB of the 227 KB)
+constexpr size_t kObSmemCap = 180 * 1024;   // dynamic part (the static part is ~40 KB of the 227 KB)
+
+// lanes given to one of n products (or sums) so that n of them fill the CTA's warps: 8, 16 or 32
+__device__ __forceinline__ int ob_lanes(int n) { return n > 32 ? 8 : (n > 16 ? 16 : 32); }
+
+// |x| as an ordered integer (the bit pattern without its sign); NaN maps to 0, as fmax ignores it
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    return u > 0x7FF0000000000000ull ? 0ull : u;
+}
+
+// The grid barrier in two halves: arrive (after every thread's prior writes) and wait, so that a CTA
+// can do local work while the other CTAs arrive.
+__device__ __forceinline__ void ob_arrive(unsigned* cnt) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(cnt), "r"(1u) : "memory");
+    }
+}
+__device__ __forceinline__ bool ob_wait(unsigned* cnt, unsigned nblocks, unsigned k, long long spin_limit, int* err,
+                                        int* ok_s) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = nblocks * (k + 1u);
+        long long it = 0;
+        while (ld_acquire_u(cnt) < target) {
+            if (++it > spin_limit) {
+                set_error(err, CSLS_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            if (it > 256) __nanosleep(32);
+        }
+        *ok_s = ok && (*(volatile int*)err != CSLS_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
 
 template <bool SMEM>
 __global__ void __launch_bounds__(kObThreads, 1)
 k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk, const int* E, double* tau,
           double* Tb, unsigned short* Vd, unsigned short* VTd, int64_t ldvp, int* frow, int* ecol, double* part,
-          unsigned* bar, long long spin, int* err) {
+          unsigned* bar, long long spin, int* err, double* wsc) {
     extern __shared__ __align__(16) double ob_dyn[];
     __shared__ double red[kRedSlots];
-    __shared__ double wk[kOB];
+    __shared__ double refl[4];   // tau, 1 / (alpha - beta), beta, alpha - beta of the current column
     __shared__ double taus[kOB];
     __shared__ double cmax[kOB];
     __shared__ double gT[kOB * kOB];   // Gram columns (strict upper part), turned into T by CTA 0
+    __shared__ double mult[kOB];   // update multipliers of the current column
+    __shared__ int ok_s;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t L = s - J0;
-    const int64_t r0 = J0 + (int64_t)g * chunk;
-    const int64_t r1 = r0 + chunk < s ? r0 + chunk : s;
+    // CTA 0 holds no rows (it forms T at the end while the others cut their digits); CTA 1 holds the
+    // block's nd = min(nbo, L) diagonal rows only (the CTA that owns them runs its loops slower per row,
+    // so it gets few); CTA g >= 2 holds rows J0 + nd + (g - 2) chunk .. + chunk - 1
+    const int64_t nd = (int64_t)nbo < L ? (int64_t)nbo : L;
+    const int64_t r0 = g == 0 ? s : (g == 1 ? J0 : J0 + nd + (int64_t)(g - 2) * chunk);
+    const int64_t r1 = g == 0 ? s : (g == 1 ? J0 + nd : (r0 + chunk < s ? r0 + chunk : s));
     const int nloc = r1 > r0 ? (int)(r1 - r0) : 0;
     long long* Af = reinterpret_cast<long long*>(A);
     double* W;
     int64_t ldw;
     if (SMEM) {
         W = ob_dyn;
-        ldw = chunk | 1;   // odd: threads reading the same row of different columns hit different banks
+        ldw = (chunk > nd ? chunk : nd) | 1;   // odd: threads reading one row of different columns hit different banks
     } else {
-        W = A + r0 + J0 * lda;
-        ldw = lda;
+        // a contiguous region of global scratch per CTA (its rows of the block, column-major): the
+        // matrix's own column stride would put a CTA's 64 column segments far apart
+        W = wsc + (r0 - J0) * kOB;
+        ldw = nloc > 0 ? nloc : 1;
     }
     // fixed point -> binary64: this CTA's rows of the block, and (grid-stride) rows 0 .. J0 - 1
     for (int c = 0; c < nbo; ++c) {
@@ -318,178 +399,223 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
     // k, k = 1..63), stored CTA-major so that a reduction reads each CTA's slots contiguously; (b) the
     // owner CTA's diagonal-row values alpha and top_k (own[0], own[k]), which need no reduction. Both
     // come in two buffers that alternate by step, so a CTA that runs ahead never overwrites values
-    // another CTA is still reading. The Gram matrix V^T V and the column maxima of V are needed only
-    // once the block is done: they are reduced once at the end.
+    // another CTA is still reading. The Gram matrix V^T V and the column maxima of V are reduced once
+    // at the end.
     constexpr int kSlots = kOB;
-    constexpr int kGramSlots = kOB * (kOB - 1) / 2 + kOB;   // strict upper Gram entries + column maxima
+    constexpr int kGram = kOB * (kOB - 1) / 2;        // strict upper Gram entries, column b at b (b - 1) / 2
+    constexpr int kGramSlots = kGram + kOB;            // then the column maxima
     double* const own_base = part + 2 * (int64_t)G * kSlots;
     double* const gram_part = own_base + 2 * (kOB + 1);      // G x kGramSlots, then the reduced entries
     double* const gram_red = gram_part + (int64_t)G * kGramSlots;
-    auto sums = [&](int step) { return part + (int64_t)(step & 1) * G * kSlots + (int64_t)g * kSlots; };
+    double* const gp = gram_part + (int64_t)g * kGramSlots;
     auto owns = [&](int step) { return own_base + (step & 1) * (kOB + 1); };
-    // Dot products over this CTA's rows: eight threads per product (thread q of the eight takes rows
-    // rs + q, rs + q + 8, ...), combined by three shuffle steps in a fixed order; a warp holds four
-    // products and skips when all four are absent. (FP64 arithmetic is the scarce resource here: each
-    // FP64 warp instruction occupies the pipe for the same time whatever its active lanes, so no warp
-    // computes placeholder products, and a warp per product over a few hundred rows would spend as many
-    // additions on its shuffle tree as on the products.)
-    auto dot8 = [&](const double* xs, const double* ys, int rs, int q) {
-        double acc = 0.0;
-        for (int r = rs + q; r < nloc; r += 8) acc += xs[r] * ys[r];
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-        return acc;
-    };
-    // partial sums that column c (global row jj = J0 + c) needs, written for step c
+
+    // partial sums that column c (global row jj = J0 + c) needs, written for step c: task 0 is sigma,
+    // task t >= 1 is d_{c+t}; P lanes a task (lane q of P takes rows rs + q, rs + q + P, ...), combined
+    // by a fixed shuffle tree; a warp whose tasks are all absent issues nothing
     auto column_sums = [&](int c) {
         const int64_t jj = J0 + c;
         const int rs = (int)(jj + 1 - r0 > 0 ? (jj + 1 - r0 < nloc ? jj + 1 - r0 : nloc) : 0);
-        double* ps = sums(c);
+        double* ps = part + (int64_t)(c & 1) * G * kSlots + (int64_t)g * kSlots;
         double* po = owns(c);
-        const int ntask = nbo - c;   // task 0: sigma; task t >= 1: d_{c+t}; at most kObThreads / 8
-        const int t = tid >> 3, q = tid & 7;
-        if (warp * 4 < ntask) {   // warp-uniform: some product of this warp is present
+        const int ntask = nbo - c;
+        const int P = ob_lanes(ntask);
+        const int t = tid / P, q = tid & (P - 1);
+        if (warp * (32 / P) < ntask) {
             const bool active = t < ntask;
-            const double acc = dot8(W + c * ldw, W + (c + (active ? t : 0)) * ldw, active ? rs : nloc, q);
+            const double* xs = W + c * ldw;
+            const double* ys = W + (c + (active ? t : 0)) * ldw;
+            double acc = 0.0;
+            for (int r = (active ? rs : nloc) + q; r < nloc; r += P) acc = fma(xs[r], ys[r], acc);
+            for (int o = 1; o < P; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (active && q == 0) {
                 ps[t == 0 ? 0 : c + t] = acc;
                 if (own(jj)) po[t == 0 ? 0 : c + t] = W[(c + t) * ldw + (jj - r0)];
             }
         }
     };
-    // Reduction at the barrier of step c: thread (phase h, slot s) sums the slot over CTAs h, h + 8,
-    // ... (independent loads, coalesced across the slots), then the eight phases are added in a fixed
-    // order; all CTAs obtain the same bits. Live slots: sigma and d_k, c < k < nbo.
-    __shared__ double red8[8][kSlots];
+    // The sums of step c: live slots sigma and d_k (c < k < nbo), P lanes a slot; lane h of P sums
+    // the slot over CTAs h, h + P, ... (independent loads), then a fixed shuffle tree; all CTAs obtain
+    // the same bits. The lane that finishes a slot also fetches the owner value (alpha or top_k), and
+    // thread 0 forms the reflector of column c right away.
     auto reduce_step = [&](int c) {
-        const int sl = tid & (kSlots - 1), h = tid >> 6;
-        const bool live = sl == 0 || (sl > c && sl < nbo);
-        double acc = 0.0;
-        if (live) {
+        const int nlive = nbo - c;
+        const int P = ob_lanes(nlive);
+        const int i = tid / P, h = tid & (P - 1);
+        if (warp * (32 / P) >= nlive) return;   // warp-uniform
+        const bool act = i < nlive;
+        const int sl = i == 0 ? 0 : c + i;
+        double ov = 0.0, acc = 0.0;
+        if (act && h == 0) ov = __ldcg(owns(c) + sl);
+        if (act) {
             const double* src = part + (int64_t)(c & 1) * G * kSlots + sl;
-            for (int q = h; q < G; q += 8) acc += __ldcg(src + (int64_t)q * kSlots);
+#pragma unroll 4
+            for (int q = h; q < G; q += P) acc += __ldcg(src + (int64_t)q * kSlots);
         }
-        red8[h][sl] = acc;
-        __syncthreads();
-        if (tid < kSlots) {
-            double v = red8[0][tid];
-#pragma unroll
-            for (int i = 1; i < 8; ++i) v += red8[i][tid];
-            if (tid == 0) red[kRedSig] = v;
-            else red[kRedD + tid] = v;
-        } else if (tid < kSlots + kOB) {
-            const int k = tid - kSlots;   // owner values of column c
-            const double v = __ldcg(owns(c) + k);
-            if (k == 0) red[kRedAlpha] = v;
-            else if (k > c && k < nbo) red[kRedTop + k] = v;
+        for (int o = 1; o < P; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (!act || h != 0) return;
+        if (i != 0) {
+            red[kRedD + sl] = acc;
+            red[kRedTop + sl] = ov;
+            return;
+        }
+        // reflector of column c: beta = -sign(alpha) sqrt(alpha^2 + sigma), tau = (beta - alpha) / beta,
+        // 1 / (alpha - beta); 1 / |beta| from one reciprocal square root
+        const double sigma = acc, alpha = ov;
+        double tau_c = 0.0, scal = 1.0, beta = alpha, amb = 1.0;
+        if (sigma != 0.0) {
+            const double n2 = fma(alpha, alpha, sigma);
+            const double rn = rsqrt(n2);
+            const double nrm = n2 * rn;
+            beta = alpha >= 0.0 ? -nrm : nrm;
+            amb = alpha - beta;   // sign(alpha) (|alpha| + nrm): never 0
+            tau_c = fabs(amb) * rn;
+            scal = __drcp_rn(amb);
+        }
+        red[kRedSig] = sigma;
+        red[kRedAlpha] = alpha;
+        refl[0] = tau_c;
+        refl[1] = scal;
+        refl[2] = beta;
+        refl[3] = amb;
+        taus[c] = tau_c;
+        if (g == 0) tau[J0 + c] = tau_c;
+    };
+    // Gram column b (a < b: G(a, b) = v_a^T v_b over this CTA's rows; v_a is 0 above its diagonal row
+    // and 1 on it, so only rows from J0 + b on contribute) and the column maximum |v_b| (with its unit
+    // entry), into this CTA's partial slots
+    auto gram_column = [&](int b) {
+        const int64_t db = J0 + b;
+        const int rd = (int)(db - r0);
+        const int rs = (int)(db - r0 > 0 ? (db - r0 < nloc ? db - r0 : nloc) : 0);
+        const int t = tid >> 3, q = tid & 7;
+        const double* vb = W + b * ldw;
+        if (warp * 4 < b) {   // warp-uniform: some entry a < b in this warp
+            const bool active = t < b;
+            const double* va = W + (active ? t : 0) * ldw;
+            double acc = 0.0;
+            for (int r = (active ? rs : nloc) + q; r < nloc; r += 8) acc = fma(va[r], r == rd ? 1.0 : vb[r], acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            if (active && q == 0) gp[b * (b - 1) / 2 + t] = acc;
+        }
+        if (warp == kObWarps - 1) {
+            unsigned long long mx = 0x3FF0000000000000ull;   // the unit entry
+            for (int r = (rs > rd + 1 ? rs : rd + 1) + lane; r < nloc; r += 32) {
+                const unsigned long long u = abs_bits(vb[r]);
+                mx = u > mx ? u : mx;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long u = __shfl_xor_sync(0xffffffffu, mx, o);
+                mx = u > mx ? u : mx;
+            }
+            if (lane == 0) gp[kGram + b] = __longlong_as_double((long long)mx);
         }
     };
 
     unsigned nbar = 0;   // barriers passed (the counter slot of this launch starts at 0)
     column_sums(0);
     for (int c = 0; c < nbo; ++c) {
-        if (!grid_sync_count(bar, G, nbar++, spin, err)) return;
+        ob_arrive(bar);
+        if (SMEM && c > 0) gram_column(c - 1);   // the block in global memory: the Gram matrix at the end
+        if (!ob_wait(bar, G, nbar++, spin, err, &ok_s)) return;
         reduce_step(c);
         __syncthreads();
         const int64_t jj = J0 + c;
-        // reflector of column c: one thread forms the scalars (FP64 division and square root are
-        // expensive on this part, so they are not repeated per thread)
-        __shared__ double refl[3];   // tau, 1 / (alpha - beta), beta
-        if (tid == 0) {
-            const double sigma = red[kRedSig], alpha = red[kRedAlpha];
-            double tau_c = 0.0, scal = 1.0, beta = alpha;
-            if (sigma != 0.0) {
-                const double nrm = sqrt(alpha * alpha + sigma);
-                beta = alpha >= 0.0 ? -nrm : nrm;
-                tau_c = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
+        const double tau_c = refl[0], scal = refl[1], beta = refl[2], amb = refl[3];
+        const bool live = red[kRedSig] != 0.0;
+        const int rj = (int)(jj - r0);   // local index of the diagonal row (may be outside [0, nloc))
+        // A(j:s, k) -= w_k v for the later block columns (rows of this CTA), with w_k = tau v^T A(j:s, k)
+        // and v = x / (alpha - beta) below the diagonal row: A(r, k) -= (w_k / (alpha - beta)) y(r) with y = x
+        // below the diagonal row and alpha - beta on it (one multiplier a column, formed once by 64 lanes,
+        // so one FMA an element); WPC warps a column when few remain
+        if (live) {
+            if (tid > c && tid < nbo) mult[tid] = -(tau_c * fma(scal, red[kRedD + tid], red[kRedTop + tid])) * scal;
+            __syncthreads();
+            const int nk = nbo - c - 1;
+            const int WPC = nk >= 16 ? 1 : (nk >= 8 ? 2 : (nk >= 4 ? 4 : (nk >= 2 ? 8 : 16)));
+            const int cpp = kObWarps / WPC;
+            const int rs = rj > 0 ? (rj < nloc ? rj : nloc) : 0;
+            const double* x = W + c * ldw;
+            for (int k = c + 1 + warp / WPC; k < nbo; k += cpp) {
+                const double nws = mult[k];
+                double* col = W + k * ldw;
+                for (int r = rs + (warp % WPC) * 32 + lane; r < nloc; r += 32 * WPC)
+                    col[r] = fma(nws, r == rj ? amb : x[r], col[r]);
             }
-            refl[0] = tau_c;
-            refl[1] = scal;
-            refl[2] = beta;
-            taus[c] = tau_c;
-            if (g == 0) tau[jj] = tau_c;
         }
         __syncthreads();
-        const double tau_c = refl[0], scal = refl[1], beta = refl[2];
-        const bool live = red[kRedSig] != 0.0;
-        if (tid < kOB) wk[tid] = (tid > c && tid < nbo) ? tau_c * (red[kRedTop + tid] + scal * red[kRedD + tid]) : 0.0;
-        const int rj = (int)(jj - r0);   // local index of the diagonal row (may be outside [0, nloc))
-        if (live) {
+        // column c becomes v (beta on the diagonal row); the next column's sums read only later columns
+        if (live)
             for (int r = tid; r < nloc; r += kObThreads) {
                 if (r > rj) W[c * ldw + r] *= scal;
                 else if (r == rj) W[c * ldw + r] = beta;
             }
-        }
-        __syncthreads();
-        // A(j:s, k) -= w_k v for the later block columns (rows of this CTA)
-        if (live) {
-            const int rs = rj > 0 ? (rj < nloc ? rj : nloc) : 0;
-            for (int k = c + 1 + warp; k < nbo; k += kObWarps) {
-                const double w = wk[k];
-                double* col = W + k * ldw;
-                const double* v = W + c * ldw;
-                for (int r = rs + lane; r < nloc; r += 32) col[r] -= w * (r == rj ? 1.0 : v[r]);
-            }
-        }
-        __syncthreads();
         if (c + 1 < nbo) column_sums(c + 1);
     }
-    // Gram matrix of V (entries a < b over this CTA's rows, v masked: 0 above its diagonal row, 1 on
-    // it) and the column maxima of |v|, a warp per entry
-    {
-        double* gp = gram_part + (int64_t)g * kGramSlots;
-        // strict upper entries, four threads per entry: e -> (a, b), a < b, b (b - 1) / 2 <= e < b (b + 1) / 2
-        const int ngram = kGramSlots - kOB;
-        for (int e0 = 0; e0 < ngram; e0 += kObThreads / 4) {
-            const int e = e0 + (tid >> 2), q = tid & 3;
-            const bool active = e < ngram;
-            int bcol = 1, acol = 0;
-            if (active) {
-                bcol = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
-                while (bcol * (bcol - 1) / 2 > e) --bcol;
-                while ((bcol + 1) * bcol / 2 <= e) ++bcol;
-                acol = e - bcol * (bcol - 1) / 2;
-            }
-            const bool real = active && bcol < nbo;
-            const int64_t db = J0 + (real ? bcol : 0);   // rows >= db carry v_b (1 on db)
-            const int rs = real ? (int)(db - r0 > 0 ? (db - r0 < nloc ? db - r0 : nloc) : 0) : nloc;
-            const int rd = (int)(db - r0);
-            const double* va = W + (real ? acol : 0) * ldw;
-            const double* vb = W + (real ? bcol : 0) * ldw;
-            double a0 = 0.0, a1 = 0.0;
-            int r = rs + q;
-            for (; r + 4 < nloc; r += 8) {
-                a0 += va[r] * (r == rd ? 1.0 : vb[r]);
-                a1 += va[r + 4] * (r + 4 == rd ? 1.0 : vb[r + 4]);
-            }
-            if (r < nloc) a0 += va[r] * (r == rd ? 1.0 : vb[r]);
-            double acc = a0 + a1;
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (active && q == 0) gp[e] = real ? acc : 0.0;
-        }
-        for (int e = ngram + warp; e < kGramSlots; e += kObWarps) {
-            {
-                const int a = e - (kGramSlots - kOB);
-                double mx = a < nbo ? 1.0 : 0.0;   // the unit diagonal entry
-                if (a < nbo) {
-                    const int64_t da = J0 + a;
-                    const int rs = (int)(da + 1 - r0 > 0 ? (da + 1 - r0 < nloc ? da + 1 - r0 : nloc) : 0);
-                    for (int r = rs + lane; r < nloc; r += 32) mx = fmax(mx, fabs(W[a * ldw + r]));
+    __syncthreads();
+    if (SMEM) gram_column(nbo - 1);
+    if (!SMEM) {
+        // the block in global memory: the Gram matrix of V once the loop is done (entries a < b over this
+        // CTA's rows, v masked: 0 above its diagonal row, 1 on it; four lanes an entry) and the column
+        // maxima of |v| (a warp a column)
+        {
+            // strict upper entries, four threads per entry: e -> (a, b), a < b, b (b - 1) / 2 <= e < b (b + 1) / 2
+            const int ngram = kGramSlots - kOB;
+            for (int e0 = 0; e0 < ngram; e0 += kObThreads / 4) {
+                const int e = e0 + (tid >> 2), q = tid & 3;
+                const bool active = e < ngram;
+                int bcol = 1, acol = 0;
+                if (active) {
+                    bcol = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
+                    while (bcol * (bcol - 1) / 2 > e) --bcol;
+                    while ((bcol + 1) * bcol / 2 <= e) ++bcol;
+                    acol = e - bcol * (bcol - 1) / 2;
                 }
-                for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                if (lane == 0) gp[e] = mx;
+                const bool real = active && bcol < nbo;
+                const int64_t db = J0 + (real ? bcol : 0);   // rows >= db carry v_b (1 on db)
+                const int rs = real ? (int)(db - r0 > 0 ? (db - r0 < nloc ? db - r0 : nloc) : 0) : nloc;
+                const int rd = (int)(db - r0);
+                const double* va = W + (real ? acol : 0) * ldw;
+                const double* vb = W + (real ? bcol : 0) * ldw;
+                double a0 = 0.0, a1 = 0.0;
+                int r = rs + q;
+                for (; r + 4 < nloc; r += 8) {
+                    a0 += va[r] * (r == rd ? 1.0 : vb[r]);
+                    a1 += va[r + 4] * (r + 4 == rd ? 1.0 : vb[r + 4]);
+                }
+                if (r < nloc) a0 += va[r] * (r == rd ? 1.0 : vb[r]);
+                double acc = a0 + a1;
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                if (active && q == 0) gp[e] = real ? acc : 0.0;
+            }
+            for (int e = ngram + warp; e < kGramSlots; e += kObWarps) {
+                {
+                    const int a = e - (kGramSlots - kOB);
+                    double mx = a < nbo ? 1.0 : 0.0;   // the unit diagonal entry
+                    if (a < nbo) {
+                        const int64_t da = J0 + a;
+                        const int rs = (int)(da + 1 - r0 > 0 ? (da + 1 - r0 < nloc ? da + 1 - r0 : nloc) : 0);
+                        for (int r = rs + lane; r < nloc; r += 32) mx = fmax(mx, fabs(W[a * ldw + r]));
+                    }
+                    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    if (lane == 0) gp[e] = mx;
+                }
             }
         }
+    }
+    if (nbo < kOB) {   // the entries of absent columns
+        for (int e = nbo * (nbo - 1) / 2 + tid; e < kGram; e += kObThreads) gp[e] = 0.0;
+        for (int b = nbo + tid; b < kOB; b += kObThreads) gp[kGram + b] = 0.0;
     }
     if (!grid_sync_count(bar, G, nbar++, spin, err)) return;
     // each CTA reduces a share of the entries over the G partials (fixed order), then all CTAs take
     // the column maxima and CTA 0 the Gram matrix
     for (int e = g * kObWarps + warp; e < kGramSlots; e += G * kObWarps) {
         double acc = 0.0;
-        const bool is_max = e >= kGramSlots - kOB;
+        const bool is_max = e >= kGram;
         for (int q = lane; q < G; q += 32) {
             const double v = __ldcg(gram_part + (int64_t)q * kGramSlots + e);
             acc = is_max ? fmax(acc, v) : acc + v;
@@ -501,31 +627,47 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
         if (lane == 0) gram_red[e] = acc;
     }
     if (!grid_sync_count(bar, G, nbar++, spin, err)) return;
-    if (tid < kOB) cmax[tid] = __ldcg(gram_red + (kGramSlots - kOB) + tid);
-    // T of the block (CTA 0): T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) (V^T V)(0:i, i)
+    if (tid < kOB) cmax[tid] = __ldcg(gram_red + kGram + tid);
+    // T of the block (CTA 0): T(i,i) = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) (V^T V)(0:i, i), right-looking.
+    // Column i of the Gram matrix is first scaled by -tau_i (G'), so T(0:i, i) = sum over b < i of
+    // T(0:i, b) G'(b, i). Thread (i, a0) keeps acc(a, i) for rows a = a0 + 8k in registers; at step b the
+    // threads of column b store it as T(:, b), then every later column adds T(0:b, b) G'(b, i). Column b
+    // of gT holds G'(0:b, b) until step b and T(0:b, b) from then on, and only the eight threads of
+    // column b touch it in between (ordered by the warp barrier).
     if (g == 0) {
-        for (int e = tid; e < kGramSlots - kOB; e += kObThreads) {
+        for (int e = tid; e < kGram; e += kObThreads) {
             int bcol = (int)((1.0 + sqrt(1.0 + 8.0 * (double)e)) * 0.5);
             while (bcol * (bcol - 1) / 2 > e) --bcol;
             while ((bcol + 1) * bcol / 2 <= e) ++bcol;
-            gT[(e - bcol * (bcol - 1) / 2) + bcol * kOB] = __ldcg(gram_red + e);
+            gT[(e - bcol * (bcol - 1) / 2) + bcol * kOB] = -taus[bcol] * __ldcg(gram_red + e);
         }
         __syncthreads();
-        // column i of T: T(a, i) = -tau_i sum_{b = a .. i-1} T(a, b) G(b, i), eight threads per row a (thread
-        // q of the eight takes b = a + q, a + q + 8, ...), combined by a fixed shuffle tree
-        const int ta = tid >> 3, tq = tid & 7;
-        for (int i = 0; i < nbo; ++i) {
-            double acc = 0.0;
-            if (ta < i)
-                for (int b = ta + tq; b < i; b += 8) acc += gT[ta + b * kOB] * gT[b + i * kOB];
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        const int ti = tid >> 3, a0 = tid & 7;
+        double acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+        for (int b = 0; b < nbo; ++b) {
+            if (ti == b) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int a = a0 + 8 * k;
+                    if (a < b) gT[a + b * kOB] = acc[k];
+                    else if (a == b) gT[a + b * kOB] = taus[b];
+                }
+            }
             __syncthreads();
-            if (ta < i && tq == 0) gT[ta + i * kOB] = -taus[i] * acc;
-            if (tid == i) gT[i + i * kOB] = taus[i];
-            __syncthreads();
+            if (ti > b && ti < nbo) {
+                const double gbi = gT[b + ti * kOB];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (8 * k <= b) {
+                        const int a = a0 + 8 * k;
+                        if (a <= b) acc[k] = fma(gT[a + b * kOB], gbi, acc[k]);
+                    }
+            }
+            __syncwarp();
         }
+        __syncthreads();
         for (int i = tid; i < kOB * kOB; i += kObThreads) {
             const int a = i % kOB, b = i / kOB;
             Tb[i] = (a <= b && b < nbo) ? gT[i] : 0.0;
@@ -541,13 +683,14 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
     __syncthreads();
     for (int r = tid; r < nloc; r += kObThreads) {
         const int64_t grow = r0 + r, lr = grow - J0;
-        double mx = 0.0;
+        unsigned long long mxb = 0ull;
         for (int a = 0; a < nbo; ++a) {
             const int64_t d = J0 + a;
             const double v = grow < d ? 0.0 : (grow == d ? 1.0 : W[a * ldw + r]);
-            mx = fmax(mx, fabs(v));
+            const unsigned long long u = abs_bits(v);
+            mxb = u > mxb ? u : mxb;
         }
-        const int f = exp_of(mx);
+        const int f = exp_of(__longlong_as_double((long long)mxb));
         frow[lr] = f;
         for (int a0 = 0; a0 < kOB; a0 += 8) {
             uint32_t pk[kDig][4];
@@ -581,7 +724,7 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
         for (int p = 0; p < kDig; ++p)
             for (int a = 0; a < kOB; ++a) VTd[vtd_index(p, a, lr)] = (unsigned short)(z & 0xFFFFu);
     }
-    if (SMEM) {   // the factored rows back to the matrix, in binary64
+    {   // the factored rows back to the matrix, in binary64
         for (int c = 0; c < nbo; ++c)
             for (int r = tid; r < nloc; r += kObThreads) A[(r0 + r) + (J0 + c) * lda] = W[c * ldw + r];
     }
@@ -1166,6 +1309,7 @@ struct EmuScratch {
     int64_t wp_elems;
     double* Wn;                   // kOB x n
     double* Tb;                   // outer block's T (kOB x kOB)
+    double* Ws;                   // the panel block when it does not fit in shared memory (s x kOB)
     unsigned* bar_cnt;            // one grid-barrier counter per outer block (zeroed per factorisation)
 };
 
@@ -1186,6 +1330,7 @@ static EmuScratch emu_carve(Carve& c, int64_t s, int64_t n) {
     e.Wp = c.take<double>((size_t)e.wp_elems);
     e.Wn = c.take<double>((size_t)(kOB * (n + kOB)));
     e.Tb = c.take<double>(kOB * kOB);
+    e.Ws = c.take<double>((size_t)(round_up(s, 32) * kOB));
     e.bar_cnt = c.take<unsigned>((size_t)ceil_div(n, kOB) + 1);
     return e;
 }
@@ -1235,10 +1380,16 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         const int64_t ldvp = round_up(L, kTcM);   // digit planes use the current block height
         // the outer block: fixed point -> binary64, Householder factorisation, T, digits of V
         {
-            int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, ceil_div(L, 128)));
-            int64_t chunk = ceil_div(L, G);
-            G = (int)ceil_div(L, chunk);
-            const size_t smem = (size_t)(chunk | 1) * nbo * sizeof(double);
+            // CTA 0 holds no rows, CTA 1 the block's nd diagonal rows, G - 2 CTAs share the other rows
+            const int64_t nd = std::min<int64_t>(nbo, L), rest = L - nd;
+            int G = 2;
+            int64_t chunk = nd;
+            if (rest > 0) {
+                const int Gr = (int)std::min<int64_t>(sms - 2, std::max<int64_t>(1, ceil_div(rest, 128)));
+                chunk = ceil_div(rest, Gr);
+                G = (int)ceil_div(rest, chunk) + 2;
+            }
+            const size_t smem = (size_t)(std::max(chunk, nd) | 1) * nbo * sizeof(double);
             const bool in_smem = smem <= ob_cap;
             int64_t J0v = J0, ldav = lda, sv = s, ldvpv = ldvp;
             int nbov = nbo;
@@ -1247,7 +1398,8 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
             double* part = q.partials;
             unsigned* bar = e.bar_cnt + (J0 / kOB);   // a zeroed counter slot per outer block
             void* args[] = {&A, &ldav, &sv, &J0v, &nbov, &chunk, (void*)&e.E, &tau, (void*)&e.Tb, (void*)&e.Vd,
-                            (void*)&e.VTd, &ldvpv, (void*)&e.frow, (void*)&e.ecol, &part, &bar, &spinv, &err};
+                            (void*)&e.VTd, &ldvpv, (void*)&e.frow, (void*)&e.ecol, &part, &bar, &spinv, &err,
+                            (void*)&e.Ws};
             // algorithmic FP64 work: Householder factorisation of the L x nbo block (2 nbo^2 (L - nbo / 3))
             // and the strict upper Gram matrix of V for T (sum over b of 2 b (L - b))
             const double fb = (double)nbo, fL = (double)L;
