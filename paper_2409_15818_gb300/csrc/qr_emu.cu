@@ -129,6 +129,20 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// a + x 2^32 (two's complement, modulo 2^64): x added to the high word
+__device__ __forceinline__ long long add_hi32(long long a, int x) {
+    long long r;
+    asm("{\n\t.reg .b32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tadd.s32 hi, hi, %2;\n\tmov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r) : "l"(a), "r"(x));
+    return r;
+}
+// a x b + c with a 64-bit product and sum
+__device__ __forceinline__ long long mad_wide_s32(int a, int b, long long c) {
+    long long r;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c));
+    return r;
+}
+
 // An integer-valued float f with |f| <= 2^22, as an int: f + 1.5 x 2^23 lies in [2^23, 2^24], where
 // the float grid is the integers, so its bit pattern is 0x4B400000 + f exactly.
 __device__ __forceinline__ int magic_int(float f) { return __float_as_int(__fadd_rn(f, kMagic)) - kMagicBits; }
@@ -1188,24 +1202,24 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
                 break;
             }
             tc::fence_after_sync();
+            // each level folds into the int64 sums with weight 2^(8 (5 - l)): levels 0 and 1 (at most
+            // 2 x 128 x 2^14 = 2^22 per window: magic-number read) add into the high word (weights 2^40
+            // and 2^32), levels 2..5 by one 32 x 32 -> 64-bit multiply-add each
 #pragma unroll 1
-            for (int l = 0; l <= kLev; ++l)
+            for (int l = 0; l <= kLev; ++l) {
+                uint32_t v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kOB * l + 32 * half), v);
+                tc::tmem_ld_wait();
+                if (l <= 1) {
+                    const int sc = l == 0 ? 256 : 1;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kOB * l + 32 * half + 16 * h), v);
-                    tc::tmem_ld_wait();
-                    // levels 0 and 1 hold at most 2 x 128 x 2^14 = 2^22 per window: magic-number read
-                    if (l <= 1) {
+                    for (int j = 0; j < 32; ++j) acc[j] = add_hi32(acc[j], magic_int(__uint_as_float(v[j])) * sc);
+                } else {
+                    const int mul = 1 << (8 * (kLev - l));
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            acc[16 * h + j] += (long long)magic_int(__uint_as_float(v[j])) << (8 * (kLev - l));
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            acc[16 * h + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << (8 * (kLev - l));
-                    }
+                    for (int j = 0; j < 32; ++j) acc[j] = mad_wide_s32(__float2int_rn(__uint_as_float(v[j])), mul, acc[j]);
                 }
+            }
             tc::fence_before_sync();
             tc::mbar_arrive(&sm.acc_empty);
         }
