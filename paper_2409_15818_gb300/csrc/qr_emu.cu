@@ -63,16 +63,17 @@ __device__ __forceinline__ void cut_digits(long long N, int (&d)[kDig]) {
     d[0] = hi >> 8;
 }
 
-// N = x 2^(47 - e) rounded to the nearest integer (ties to even), for |x| < 2^e, from the bit pattern
-// of x alone (integer instructions; FP64 ones are scarce on this part): x = m 2^e2 with the 53-bit
-// significand m, so N = m 2^-sh with sh = e - 47 - e2 >= 5 for normal x, and a right shift with
-// round-to-nearest-even gives it exactly (the same integer as rounding the exact product).
-__device__ __forceinline__ long long fix47(double x, int e) {
+// N = x 2^(BITS - e) rounded to the nearest integer (ties to even), for |x| < 2^e, from the bit
+// pattern of x alone (integer instructions; FP64 ones are scarce on this part): x = m 2^e2 with the
+// 53-bit significand m, so N = m 2^-sh with sh = e - BITS - e2, and a shift with round-to-nearest-even
+// gives it exactly (the same integer as rounding the exact product; |N| < 2^BITS).
+template <int BITS>
+__device__ __forceinline__ long long fix_bits(double x, int e) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int ev = (int)((b >> 52) & 0x7FF);
     unsigned long long m = b & 0xFFFFFFFFFFFFFull;
     if (ev != 0) m |= 1ull << 52;
-    const int sh = e - kNumBits - ((ev != 0 ? ev : 1) - 1075);
+    const int sh = e - BITS - ((ev != 0 ? ev : 1) - 1075);
     unsigned long long q;
     if (sh <= 0) {
         q = sh > -64 ? m << (-sh) : 0ull;
@@ -88,7 +89,7 @@ __device__ __forceinline__ long long fix47(double x, int e) {
 
 // digits of x relative to scale 2^e (|x| < 2^e)
 __device__ __forceinline__ void digits_f64(double x, int e, int (&d)[kDig]) {
-    cut_digits(fix47(x, e), d);
+    cut_digits(fix_bits<kNumBits>(x, e), d);
 }
 
 // digits of a fixed-point entry (|Cfix| < 2^62): N = round(Cfix / 2^(62 - 47))
@@ -125,6 +126,12 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {
     // (one integer add, one float subtract), then the top 16 bits are the bf16 pattern.
     const float f = __int_as_float(kMagicBits + v) - kMagic;
     return (unsigned short)(__float_as_uint(f) >> 16);
+}
+
+// |x| as an ordered integer (the bit pattern without its sign); NaN maps to 0, as fmax ignores it
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    return u > 0x7FF0000000000000ull ? 0ull : u;
 }
 
 __device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -169,14 +176,14 @@ __global__ void __launch_bounds__(256) k_col_exponent(const double* A, int64_t l
     }
 }
 
-// In place: SA (double) -> fixed point (int64) per column.
+// In place: SA (double) -> fixed point (int64) per column, N = round(v 2^(62 - E_c)) by integer operations.
 __global__ void k_to_fixed(double* A, int64_t lda, int64_t s, int64_t n, const int* E) {
     for (int64_t c = blockIdx.y; c < n; c += gridDim.y) {
-        const int sh = kFixBits - E[c];
+        const int ec = E[c];
         long long* colf = reinterpret_cast<long long*>(A + c * lda);
         for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < s; r += (int64_t)gridDim.x * blockDim.x) {
             const double v = A[r + c * lda];
-            colf[r] = E[c] > -1000 ? __double2ll_rn(ldexp(v, sh)) : 0LL;
+            colf[r] = ec > -1000 ? fix_bits<kFixBits>(v, ec) : 0LL;
         }
     }
 }
@@ -216,10 +223,11 @@ __device__ __forceinline__ int64_t wd_chunk(int q, int64_t c, int kg) {
 }
 
 // Wn = -T^T (sum of the split-K partials of W = V^T C) for the outer block (T: nbo x nbo upper
-// triangular, column-major with ld kOB); Wp[k] and Wn are kOB x nprime row-major. A CTA owns 64
-// columns: it sums their partials (coalesced along the columns) into shared memory, then each
-// thread forms entries of -T^T W from the shared copies of T and W.
-constexpr int kWrCols = 64;
+// triangular, column-major with ld kOB); Wp[k] and Wn are kOB x nprime row-major. A CTA owns 16
+// columns (several CTAs share an SM, so their FP64 dot products hide each other's latency): it sums
+// their partials (coalesced along the columns) into shared memory, then each thread forms entries of
+// -T^T W from the shared copies of T and W.
+constexpr int kWrCols = 16;
 constexpr size_t kWrSmem = sizeof(double) * (kOB * kOB + kOB * kWrCols);
 
 __global__ void __launch_bounds__(256) k_wreduce_ob(const double* Wp, int ks, const double* Tb, int nbo, double* Wn,
@@ -242,9 +250,14 @@ __global__ void __launch_bounds__(256) k_wreduce_ob(const double* Wp, int ks, co
         const int a = i / kWrCols, cl = i % kWrCols;
         const int64_t c = c0 + cl;
         if (a >= nbo || c >= nprime) continue;
-        double t = 0.0;
-        for (int b = 0; b <= a; ++b) t += Ts[b + a * kOB] * Ws[b * kWrCols + cl];
-        Wn[(int64_t)a * nprime + c] = -t;
+        double t = 0.0, t1 = 0.0;
+        int b = 0;
+        for (; b + 1 <= a; b += 2) {
+            t = fma(Ts[b + a * kOB], Ws[b * kWrCols + cl], t);
+            t1 = fma(Ts[b + 1 + a * kOB], Ws[(b + 1) * kWrCols + cl], t1);
+        }
+        if (b <= a) t = fma(Ts[b + a * kOB], Ws[b * kWrCols + cl], t);
+        Wn[(int64_t)a * nprime + c] = -(t + t1);
     }
 }
 
@@ -254,10 +267,13 @@ __global__ void __launch_bounds__(256) k_wreduce_ob(const double* Wp, int ks, co
 __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw, unsigned short* Wd, const int* E,
                           int64_t jc, int* gsh) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ldw; c += (int64_t)gridDim.x * blockDim.x) {
-        double mx = 0.0;
+        unsigned long long mxb = 0ull;
         for (int a = 0; a < nbo; ++a)
-            if (c < nprime) mx = fmax(mx, fabs(Wn[(int64_t)a * nprime + c]));
-        const int g = exp_of(mx);
+            if (c < nprime) {
+                const unsigned long long u = abs_bits(Wn[(int64_t)a * nprime + c]);
+                mxb = u > mxb ? u : mxb;
+            }
+        const int g = exp_of(__longlong_as_double((long long)mxb));
         gsh[c] = c < nprime ? g - E[jc + c] + kFixBits - 14 - 8 * kLev : 0;
         for (int a0 = 0; a0 < kOB; a0 += 8) {   // 16-byte chunks of 8 K-consecutive digits
             uint32_t pk[kDig][4];
@@ -321,12 +337,6 @@ constexpr size_t kObSmemCap = 180 * 1024;   // dynamic part (the static part is 
 
 // lanes given to one of n products (or sums) so that n of them fill the CTA's warps: 8, 16 or 32
 __device__ __forceinline__ int ob_lanes(int n) { return n > 32 ? 8 : (n > 16 ? 16 : 32); }
-
-// |x| as an ordered integer (the bit pattern without its sign); NaN maps to 0, as fmax ignores it
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-    return u > 0x7FF0000000000000ull ? 0ull : u;
-}
 
 // The grid barrier in two halves: arrive (after every thread's prior writes) and wait, so that a CTA
 // can do local work while the other CTAs arrive.
@@ -1454,7 +1464,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
         CSLS_CUDA(cudaGetLastError());
         // digits of Wn, then the exact update
         const int64_t ldwp = round_up(nprime, kTcN);
-        k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 256)), 256, 0, st>>>(e.Wn, nbo, nprime, ldwp, e.Wd,
+        k_wdigits<<<(unsigned)std::max<int64_t>(1, ceil_div(ldwp, 128)), 128, 0, st>>>(e.Wn, nbo, nprime, ldwp, e.Wd,
                                                                                         e.E, J0 + nbo, e.gsh);
         CSLS_CUDA(cudaGetLastError());
         // a trailing block exists only right of a full 64-column outer block: the update's
