@@ -169,8 +169,8 @@ int csls_sketch(const csls_csr* A, int64_t s, uint64_t seed, int prec, void* SA,
  * scratch needs exceed 16 MiB (roughly 4 m + 16 s bytes) are rejected with
  * CSLS_ERR_WORKSPACE before any device work; use csls_sketch for those.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress with that device current); make that first call before
- * any stream capture. All calls share the one array and each call starts by
+ * (cudaGetSymbolAddress with that device current). All calls share the one
+ * array and each call starts by
  * clearing what must start at zero, so calls that overlap on the GPU (different
  * streams, or different host threads on the same device) race and must be
  * serialised by the caller. Arguments, layout and results are those of
