@@ -447,6 +447,23 @@ def test_emulated_factor_odd_sketch_height(csls, m, n, s):
     assert np.all(np.diag(R) >= 0) and np.all(np.tril(R, -1) == 0)
 
 
+@pytest.mark.parametrize("m,n,s", [(2000, 130, 130), (700, 192, 200)])
+def test_emulated_factor_short_outer_blocks(csls, m, n, s):
+    # s at or just above n: the last outer blocks have L <= 64 rows below their first column, so the
+    # panel's CTA that holds the block's diagonal rows holds every row (and the grid shrinks to two
+    # CTAs), or the rows past the diagonal ones fill one short chunk
+    rng = np.random.default_rng(7 * m + n)
+    A = random_sparse(m, n, 12, rng)
+    R = csls.csls_factor(dev(csls, A), s=s, seed=17, prec="f64emu").R().cpu().numpy()
+    h, d = oracle.hash_rows(m, s, 17)
+    SA = oracle.sketch(A, s, h, d)
+    assert np.linalg.norm(R.T @ R - SA.T @ SA) / np.linalg.norm(SA) ** 2 < 1e-11
+    assert np.all(np.diag(R) >= 0) and np.all(np.tril(R, -1) == 0)
+    # R itself moves by up to cond(SA) x the backward error (cond 2.4e3 and 1.9e2 here)
+    Ro = oracle.factor(A, s, 17)["R"]
+    assert _rel(R, Ro) < 1e-8
+
+
 @pytest.mark.parametrize("case", ["cfg1", "ragged_rfm"])
 def test_emulated_factor_rfm_backward_error_and_solve(csls, case):
     p = SKETCH_CASES[case]()
