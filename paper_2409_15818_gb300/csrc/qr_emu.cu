@@ -333,7 +333,11 @@ constexpr int kObThreads = 512;
 constexpr int kObWarps = kObThreads / 32;
 // reduced values of a step: sigma, alpha, d_k (64), top_k (64)
 constexpr int kRedSig = 0, kRedAlpha = 1, kRedD = 2, kRedTop = 2 + kOB, kRedSlots = 2 + 2 * kOB;
-constexpr size_t kObSmemCap = 180 * 1024;   // dynamic part (the static part is ~40 KB of the 227 KB)
+constexpr size_t kObSmemCap = 188 * 1024;   // dynamic part (the static part is ~36 KB of the 227 KB)
+
+// Row stride of the block in shared memory: at least `rows`, and 8 mod 16 in doubles, so that the two
+// columns a half-warp reads in the eight-lane dot products (columns ldw apart) fall on distinct banks.
+__host__ __device__ __forceinline__ int64_t ob_ldw(int64_t rows) { return (rows + 15) / 16 * 16 + 8; }
 
 // lanes given to one of n products (or sums) so that n of them fill the CTA's warps: 8, 16 or 32
 __device__ __forceinline__ int ob_lanes(int n) { return n > 32 ? 8 : (n > 16 ? 16 : 32); }
@@ -394,7 +398,7 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
     int64_t ldw;
     if (SMEM) {
         W = ob_dyn;
-        ldw = (chunk > nd ? chunk : nd) | 1;   // odd: threads reading one row of different columns hit different banks
+        ldw = ob_ldw(chunk > nd ? chunk : nd);
     } else {
         // a contiguous region of global scratch per CTA (its rows of the block, column-major): the
         // matrix's own column stride would put a CTA's 64 column segments far apart
@@ -1413,7 +1417,7 @@ int qr_factor_f64_emu(double* A, int64_t lda, int64_t s, int64_t n, const QrScra
                 chunk = ceil_div(rest, Gr);
                 G = (int)ceil_div(rest, chunk) + 2;
             }
-            const size_t smem = (size_t)(std::max(chunk, nd) | 1) * nbo * sizeof(double);
+            const size_t smem = (size_t)ob_ldw(std::max(chunk, nd)) * nbo * sizeof(double);
             const bool in_smem = smem <= ob_cap;
             int64_t J0v = J0, ldav = lda, sv = s, ldvpv = ldvp;
             int nbov = nbo;
