@@ -319,11 +319,16 @@ __global__ void k_wdigits(const double* Wn, int nbo, int64_t nprime, int64_t ldw
 //    lanes a slot by the number of live slots); thread 0 forms the reflector's scalars as soon as
 //    sigma is summed, with one reciprocal square root and one reciprocal;
 //  * dot products and the update spread over more lanes (and more warps) as the block's remaining
-//    columns shrink, so every sub-partition keeps work;
+//    columns shrink, so every sub-partition keeps work; the update's multipliers are formed once a
+//    column by 64 lanes, and the update is one FMA an element;
 //  * column c stays unscaled while the later columns are updated (the update uses w / (alpha -
 //    beta) on x), and becomes v in the same pass that forms the next column's sums;
 //  * each CTA arrives at the barrier of step c, then computes the Gram column V(:, 0:b)^T v_b and
-//    the maximum |v_b| of the finished column b = c - 1 over its rows, and only then waits.
+//    the maximum |v_b| of the finished column b = c - 1 over its rows, and only then waits (when the
+//    block sits in global scratch instead of shared memory, the Gram matrix is formed after the loop).
+// CTA 0 holds no rows and CTA 1 only the block's diagonal rows (the CTA that owns them runs its loops
+// slower per row); the others share the rest. When the block does not fit in shared memory, each CTA
+// keeps its rows in a contiguous region of global scratch.
 // The Gram matrix V^T V and the column maxima are reduced once at the end; CTA 0 forms T of the
 // compact WY form from them (right-looking: T(0:i, i) = -tau_i sum_b T(0:i, b) G(b, i), each
 // column of T added into the later ones as soon as it is final), every CTA writes its rows of V / R
