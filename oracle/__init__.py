@@ -116,7 +116,7 @@ def r_factor(M):
     """Sign-normalised (non-negative diagonal) R of M, in binary64."""
     F, _ = householder_qr(M)
     n = F.shape[1]
-    F64 = np.array(F, dtype=np.float64, order="F")
+    F64 = np.asfortranarray(F, dtype=np.float64)   # no second copy of a binary64 factor
     R = np.empty((n, n), dtype=np.float64, order="F")
     _load().orc_extract_r(n, _p(F64), F64.shape[0], _p(R), n)
     return R
