@@ -1010,15 +1010,16 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
 // output, sum_l T_l 2^(8 (5 - l)). That int64 stays below 2^54 sqrt(rows) (Cauchy-Schwarz with
 // |N_v| < 2^47 and sum_r N_c(r)^2 < 2^94 from the column-norm scale), so chunks of up to 2^14 rows
 // cannot overflow it.
-// Roles (448 threads):
+// Roles (704 threads):
 //   warp 0 (one thread)  copies: per K-block of 32 rows the raw int64 C rows (two 16-row x 128-
 //                        column tensor boxes, 128-byte swizzle) and the block's V digits (one 24 KB
 //                        bulk copy; the panel kernel writes them in this K-major core-matrix order);
 //   warp 1 (one thread)  the MMAs, two stages of operands;
 //   warps 2..5           cut the raw C rows into six bf16 digit planes in shared memory (one C
 //                        column per thread, read through the swizzle without bank conflicts);
-//   warps 6..13          drain the TMEM level sums every window into int64 registers (one C
-//                        column per thread and 32 V columns) and write the chunk's partial W.
+//   warps 6..21          drain the TMEM level sums every window into int64 registers (one C
+//                        column per thread and 16 V columns, four warps on each TMEM lane
+//                        quarter) and write the chunk's partial W.
 // Every wait is bounded (spin polls and wall time); a role that gives up sets the abort flag and
 // the error word; copies and MMAs in flight are still awaited (wall time only) before the CTA frees
 // its tensor memory and exits.
@@ -1030,7 +1031,8 @@ constexpr int kVcPlaneA = kVcM * kVcKB * 2;         // 8 KB: one C-digit plane o
 constexpr int kVcBBytes = kVcNStack * kVcKB * 2;    // 24 KB: the stacked V digits of a K-block
 constexpr int kVcRawBox = 16;                       // rows per raw-C tensor box (128 bytes)
 constexpr int kVcRawBytes = kVcM * kVcKB * 8;       // 32 KB of raw C per K-block
-constexpr int kVcCutWarps = 4, kVcDrainWarps = 8;
+constexpr int kVcCutWarps = 4, kVcDrainWarps = 16;
+constexpr int kVcDrainCols = 4 * kOB / kVcDrainWarps;   // V columns a drain thread folds (16)
 constexpr int kVcThreads = 32 * (2 + kVcCutWarps + kVcDrainWarps);
 constexpr int kVcMaxChunk = 1 << 14;                // rows per chunk (int64 accumulator bound)
 
@@ -1043,7 +1045,8 @@ struct VcSmem {
     int abort;
 };
 
-__global__ void __maxnreg__(144)
+// 704 threads: 22 warps put 6 on two sub-partitions, whose 16,384 registers then allow 80 a thread
+__global__ void __maxnreg__(80)
 k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* VTd, int64_t J0, int nbo, int64_t L,
              int64_t kc, const int* ecol, const int* E, double* Wp, int64_t nprime, long long spin, int* err) {
     extern __shared__ __align__(1024) unsigned char vc_smem_raw[];
@@ -1205,12 +1208,13 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
             tc::mbar_arrive(&sm.empty_raw[st]);
         }
     } else {
-        // drain: TMEM lanes 32 (warp % 4) .. + 31, V columns 32 half .. + 31
-        const int quarter = warp & 3, half = (warp - 2 - kVcCutWarps) >> 2;
+        // drain: TMEM lanes 32 (warp % 4) .. + 31, V columns 16 grp .. + 15 (four warps on each lane
+        // quarter, so their TMEM loads and folds overlap)
+        const int quarter = warp & 3, grp = (warp - 2 - kVcCutWarps) >> 2;
         const int m = quarter * 32 + lane;
-        long long acc[32];
+        long long acc[kVcDrainCols];
 #pragma unroll
-        for (int a = 0; a < 32; ++a) acc[a] = 0;
+        for (int a = 0; a < kVcDrainCols; ++a) acc[a] = 0;
         bool ok_all = true;
         for (int w = 0; w < nwin; ++w) {
             bool ok = tc::mbar_wait(&sm.acc_full, w & 1, spin, kTcWaitNs, abort);
@@ -1226,17 +1230,18 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
             // and 2^32), levels 2..5 by one 32 x 32 -> 64-bit multiply-add each
 #pragma unroll 1
             for (int l = 0; l <= kLev; ++l) {
-                uint32_t v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kOB * l + 32 * half), v);
+                uint32_t v[kVcDrainCols];
+                tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kOB * l + kVcDrainCols * grp), v);
                 tc::tmem_ld_wait();
                 if (l <= 1) {
                     const int sc = l == 0 ? 256 : 1;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] = add_hi32(acc[j], magic_int(__uint_as_float(v[j])) * sc);
+                    for (int j = 0; j < kVcDrainCols; ++j) acc[j] = add_hi32(acc[j], magic_int(__uint_as_float(v[j])) * sc);
                 } else {
                     const int mul = 1 << (8 * (kLev - l));
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] = mad_wide_s32(__float2int_rn(__uint_as_float(v[j])), mul, acc[j]);
+                    for (int j = 0; j < kVcDrainCols; ++j)
+                        acc[j] = mad_wide_s32(__float2int_rn(__uint_as_float(v[j])), mul, acc[j]);
                 }
             }
             tc::fence_before_sync();
@@ -1249,8 +1254,8 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
             if (col < nprime) {
                 const int ec = E[jc + col];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int a = 32 * half + j;
+                for (int j = 0; j < kVcDrainCols; ++j) {
+                    const int a = kVcDrainCols * grp + j;
                     if (a < nbo) out[(int64_t)a * nprime + col] = ldexp((double)acc[j], ecol[a] + ec - 54);
                 }
             }
