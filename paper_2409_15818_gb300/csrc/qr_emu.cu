@@ -1228,20 +1228,25 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
             // each level folds into the int64 sums with weight 2^(8 (5 - l)): levels 0 and 1 (at most
             // 2 x 128 x 2^14 = 2^22 per window: magic-number read) add into the high word (weights 2^40
             // and 2^32), levels 2..5 by one 32 x 32 -> 64-bit multiply-add each
+            // two levels a TMEM wait (three waits a window)
+            const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kVcDrainCols * grp);
 #pragma unroll 1
-            for (int l = 0; l <= kLev; ++l) {
-                uint32_t v[kVcDrainCols];
-                tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kOB * l + kVcDrainCols * grp), v);
+            for (int l = 0; l <= kLev; l += 2) {
+                uint32_t v[kVcDrainCols], u[kVcDrainCols];
+                tc::tmem_ld16(tq + (uint32_t)(kOB * l), v);
+                tc::tmem_ld16(tq + (uint32_t)(kOB * (l + 1)), u);
                 tc::tmem_ld_wait();
-                if (l <= 1) {
-                    const int sc = l == 0 ? 256 : 1;
+                if (l == 0) {
 #pragma unroll
-                    for (int j = 0; j < kVcDrainCols; ++j) acc[j] = add_hi32(acc[j], magic_int(__uint_as_float(v[j])) * sc);
+                    for (int j = 0; j < kVcDrainCols; ++j)
+                        acc[j] = add_hi32(acc[j], magic_int(__uint_as_float(v[j])) * 256 + magic_int(__uint_as_float(u[j])));
                 } else {
                     const int mul = 1 << (8 * (kLev - l));
 #pragma unroll
-                    for (int j = 0; j < kVcDrainCols; ++j)
+                    for (int j = 0; j < kVcDrainCols; ++j) {
                         acc[j] = mad_wide_s32(__float2int_rn(__uint_as_float(v[j])), mul, acc[j]);
+                        acc[j] = mad_wide_s32(__float2int_rn(__uint_as_float(u[j])), mul >> 8, acc[j]);
+                    }
                 }
             }
             tc::fence_before_sync();
