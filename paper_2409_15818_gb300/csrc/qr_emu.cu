@@ -1236,6 +1236,10 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
                 tc::tmem_ld16(tq + (uint32_t)(kOB * l), v);
                 tc::tmem_ld16(tq + (uint32_t)(kOB * (l + 1)), u);
                 tc::tmem_ld_wait();
+                if (l + 2 > kLev) {   // the window's last TMEM reads are done: the MMAs may go on while this folds
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&sm.acc_empty);
+                }
                 if (l == 0) {
 #pragma unroll
                     for (int j = 0; j < kVcDrainCols; ++j)
@@ -1249,8 +1253,6 @@ k_emu_vtc_tc(const __grid_constant__ CUtensorMap rawmap, const unsigned short* V
                     }
                 }
             }
-            tc::fence_before_sync();
-            tc::mbar_arrive(&sm.acc_empty);
         }
         if (ok_all) {
             // W(a, c) = acc 2^(e_a + E_c - 54) (V digits carry 2^(e_a - 47), C digits 2^(E_c - 47), acc 2^-40)
