@@ -778,9 +778,11 @@ k_obpanel(double* A, int64_t lda, int64_t s, int64_t J0, int nbo, int64_t chunk,
 //                        sets of 6 x 32 columns, so the MMAs of tile i + 1 run while tile i is
 //                        written back;
 //   warps 2..17          epilogue: TMEM -> registers, levels combined in int64, scaled onto the
-//                        column's fixed-point grid and added to the staged C entry; one thread
-//                        per row and 8 columns, so each column store of a warp is 256
-//                        contiguous bytes.
+//                        column's fixed-point grid and added into the staged C block in shared
+//                        memory (one thread per row and 8 columns); warp 0 writes the block back
+//                        with one 2D tensor store (outside the matrix nothing is written) before
+//                        the stage takes the next C block, and fetches the block two tiles ahead
+//                        into L2.
 // Every wait is bounded (spin polls and 2 s of wall time); a role that gives up sets the CTA's
 // abort flag and the error word, and the CTA still waits for its copies and MMAs in flight and
 // frees its tensor memory before it returns.
@@ -812,6 +814,23 @@ __device__ __forceinline__ void tensor_g2s_2d(void* dst, const CUtensorMap* map,
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(tc::smem_addr(bar))
         : "memory");
 }
+
+// 2D tiled tensor copy shared -> global (the box at coordinates x, y; parts outside the tensor are not
+// written), as one bulk group; the box at x, y into L2 only; and the waits for this thread's bulk
+// groups: reads of shared memory done, or the whole copy done
+__device__ __forceinline__ void tensor_s2g_2d(const void* src, const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n"
+                 "cp.async.bulk.commit_group;" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(tc::smem_addr(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tensor_prefetch_l2_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64_t lda, int64_t s, int64_t J0, int nbo,
@@ -854,13 +873,15 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
         if (lane == 0) {
             // uses of each stage whose B (Wn digits) and C copies were issued
             int armedB0 = 0, armedB1 = 0, armedC0 = 0, armedC1 = 0;
+            int stored = 0;   // tiles written back by a tensor store
             tc::mbar_arrive_expect_tx(&sm.full_a, kDig * kTcPlaneA);
             tc::bulk_g2s(sm.A[0], reinterpret_cast<const unsigned char*>(Vd) + rt * (kDig * kTcPlaneA),
                          kDig * kTcPlaneA, &sm.full_a);
             for (int i = 0; i < ntile; ++i) {
                 const int b = i & 1, u = i >> 1;
                 // stage b's Wn digits are free once tile i - 2's accumulators were read (its MMAs are
-                // done); its C block once tile i - 2's write-back has read it
+                // done); its C block once tile i - 2's updated values, folded into it by the epilogue,
+                // have been read out by that tile's tensor store
                 if (u > 0 && !tc::mbar_wait(&sm.tfree[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
                     *abort = 1;
                     set_error(err, CSLS_ERR_TIMEOUT);
@@ -872,16 +893,35 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                              kDig * kTcPlaneB, &sm.full_b[b]);
                 if (b) armedB1 = u + 1;
                 else armedB0 = u + 1;
-                if (u > 0 && !tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
+                if (u > 0) {
+                    if (!tc::mbar_wait(&sm.freed[b], (u - 1) & 1, spin, kTcWaitNs, abort)) {
+                        *abort = 1;
+                        set_error(err, CSLS_ERR_TIMEOUT);
+                        break;
+                    }
+                    tensor_s2g_2d(sm.C[b][0], &cmap, (int)(J0 + rb), (int)(jc + (ct - 2) * kTcN));
+                    ++stored;
+                    bulk_wait_read_all();
+                }
+                tc::mbar_arrive_expect_tx(&sm.full_c[b], kTcN * kTcM * 8);
+                tensor_g2s_2d(sm.C[b][0], &cmap, (int)(J0 + rb), (int)(jc + ct * kTcN), &sm.full_c[b]);
+                // two stages hold only about one C block in flight per SM: tile i + 2's block is fetched
+                // into L2 now, so its copy into shared memory (after tile i's write-back) hits L2
+                if (i + 2 < ntile) tensor_prefetch_l2_2d(&cmap, (int)(J0 + rb), (int)(jc + (ct + 2) * kTcN));
+                if (b) armedC1 = u + 1;
+                else armedC0 = u + 1;
+            }
+            // the last tiles' write-backs (tiles stored .. ntile - 1, one per stage)
+            for (int t = stored; t < ntile && !*abort; ++t) {
+                const int b = t & 1, u = t >> 1;
+                if (!tc::mbar_wait(&sm.freed[b], u & 1, spin, kTcWaitNs, abort)) {
                     *abort = 1;
                     set_error(err, CSLS_ERR_TIMEOUT);
                     break;
                 }
-                tc::mbar_arrive_expect_tx(&sm.full_c[b], kTcN * kTcM * 8);
-                tensor_g2s_2d(sm.C[b][0], &cmap, (int)(J0 + rb), (int)(jc + ct * kTcN), &sm.full_c[b]);
-                if (b) armedC1 = u + 1;
-                else armedC0 = u + 1;
+                tensor_s2g_2d(sm.C[b][0], &cmap, (int)(J0 + rb), (int)(jc + (ct0 + t) * kTcN));
             }
+            bulk_wait_all();   // tensor stores complete before the CTA leaves
             // copies in flight land before the CTA can leave. Issued copies always complete, so
             // these waits are bounded by wall time only (not by the caller's spin count, which
             // may be tiny): a CTA never exits with a copy still writing its shared memory.
@@ -942,7 +982,6 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
         const int64_t lr = rb + r;
         const bool rok = lr < L;
         const int fr = rok ? frow[lr] : 0;
-        long long* const crow = Cfix + (J0 + lr) + jc * lda;   // this thread's row of the trailing block
         for (int i = 0; i < ntile; ++i) {
             const int b = i & 1, u = i >> 1;
             bool ok = tc::mbar_wait(&sm.done[b], u & 1, spin, kTcWaitNs, abort) &&
@@ -984,9 +1023,11 @@ k_emu_update_tc(const __grid_constant__ CUtensorMap cmap, long long* Cfix, int64
                     long long dlt;
                     if (sh >= 0) dlt = sh < 63 ? acc << sh : 0;
                     else dlt = -sh < 63 ? (acc + (1LL << (-sh - 1))) >> (-sh) : 0;
-                    crow[col * lda] = sm.C[b][part * kTcEpiCols + j][r] + dlt;
+                    sm.C[b][part * kTcEpiCols + j][r] += dlt;   // written back by the tile's tensor store
                 }
             }
+            // generic-proxy shared-memory writes become visible to the tensor store (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc::mbar_arrive(&sm.freed[b]);
         }
     }
