@@ -188,12 +188,12 @@ def replica_problem(config, rank):
 # outer block 40: L = 26,240 rows, n' = 4,576 trailing columns) times the units of an average bench launch
 # (2.869e6 panel elements; 3.006e8 trailing-product elements). Traffic grows in proportion to these units:
 # the products stream C once (vtc) or twice (update), the panel reads its block once.
-TRAFFIC = {"k_obpanel": 12.28 * 2.869e6, "k_emu_vtc_tc": 8.196 * 3.006e8, "k_emu_update_tc": 15.871 * 3.006e8}
+TRAFFIC = {"k_obpanel": 12.28 * 2.869e6, "k_emu_vtc_tc": 8.199 * 3.006e8, "k_emu_update_tc": 15.875 * 3.006e8}
 _TSRC = ("profiles/%s_rfm6x6.md (ncu --set full, launch 41 of the 6x6-box workload): %.3f B per %s, scaled to an "
          "average launch of the 2D bench workload")
 TRAFFIC_SOURCE = {"k_obpanel": _TSRC % ("obpanel", 12.28, "panel element (L x 64)"),
-                  "k_emu_vtc_tc": _TSRC % ("emu_vtc_tc", 8.196, "trailing element (L x n'; algorithmic 8)"),
-                  "k_emu_update_tc": _TSRC % ("emu_update_tc", 15.871, "trailing element (L x n'; algorithmic 16)")}
+                  "k_emu_vtc_tc": _TSRC % ("emu_vtc_tc", 8.199, "trailing element (L x n'; algorithmic 8)"),
+                  "k_emu_update_tc": _TSRC % ("emu_update_tc", 15.875, "trailing element (L x n'; algorithmic 16)")}
 
 
 def oracle_cache(p, config):
