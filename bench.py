@@ -29,6 +29,7 @@ WORKLOADS = {
     "cfg4a": "2D Poisson RFM cfg2 matrix with 64 right-hand sides sin(a pi x) sin(b pi y), block LSQR, s=4n",
     "cfg5": "random sparse 2e6 x 2e4, 10/row, columns scaled over 10 decades, s=4n",
     "rfm6x6": "2D Poisson RFM, 6x6 boxes, J=200, 30x30 points/box, m=36720 n=7200 nnz=8.06M, s=4n",
+    "rfm6x6_64": "2D Poisson RFM rfm6x6 matrix with 64 right-hand sides sin(a pi x) sin(b pi y), block LSQR, s=4n",
     "cfg4b": "32 uneven 2D Poisson RFM instances (grids 2x2..6x6, J in {50,100,150}, 15..25 points/side), "
              "factored one by one, solved in one CUDA-graph launch",
 }

@@ -17,6 +17,8 @@ namespace csls {
 constexpr int kBT = 256;       // threads
 constexpr int kNR = 8;         // right-hand sides per triangular-solve CTA
 constexpr int kTB = kTrsvBlock;
+constexpr int kKQ = 4;        // quarters of a block's k range per triangular-solve CTA
+constexpr int kKW = kTB / kKQ; // k entries of a quarter
 
 struct BlockCtl {
     TrsvCtl up, lo;
@@ -159,6 +161,10 @@ __device__ __forceinline__ bool wait_flag_b(const int* flag, int want, long long
 
 // Z = R^{-1} (V diag(1/alpha)) for the live columns, with the x / wx epilogue.
 // CTA = (ticket k) -> block row b = nb - 1 - k / ngroups, column group g = k % ngroups.
+// Thread (row, kq) of a CTA owns row `row` of the block and the quarter kq of each 64-column block of R
+// it multiplies: per block, its 16 entries of R are loaded before the wait for that block's solution
+// (they do not depend on it), the group's 64 x 8 solution block is staged in shared memory, and each R
+// entry meets all 8 columns (8 independent FMA chains). The four quarters are summed in a fixed order.
 template <class TR>
 __global__ void __launch_bounds__(kBT)
 k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const double* __restrict__ Dinv, int W,
@@ -166,7 +172,9 @@ k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
                  long long spin, int* err) {
     __shared__ int tk_s;
     __shared__ unsigned epoch_s;
-    __shared__ double rhs[kTB][kNR];
+    __shared__ double zs[kTB][kNR];             // the solution block being multiplied (group columns)
+    __shared__ double part[kKQ][kTB][kNR + 1];  // per-quarter partial sums (padded rows: no bank conflicts)
+    __shared__ double rhs[kTB][kNR + 1];
     __shared__ double cf[kNR][4];   // 1/alpha, cx, cw, first (0 for converged columns)
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -187,56 +195,84 @@ k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
     const int want = (int)(epoch_s + 1u);
     const int64_t r0 = (int64_t)b * kTB;
     const int bs = (int)(n - r0 < kTB ? n - r0 : kTB);
-    const int row = tid & (kTB - 1), cp = tid >> 6;    // columns c0g + 2cp, +1
-    double acc0 = 0.0, acc1 = 0.0;
+    const int row = tid & (kTB - 1), kq = tid >> 6;       // row of the block, quarter of the k range
+    const int zk = tid >> 1, zj = (tid & 1) * 4;          // staging: threads 0..127, 4 values each
+    double acc[kNR];
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) acc[j] = 0.0;
     for (int c = nb - 1; c > b; --c) {
         const int64_t cc0 = (int64_t)c * kTB;
         const int cs = (int)(n - cc0 < kTB ? n - cc0 : kTB);
+        double r[kKW];
+        {
+            const TR* rp = R + (r0 + row) + (cc0 + kq * kKW) * n;
+#pragma unroll
+            for (int kk = 0; kk < kKW; ++kk)
+                r[kk] = (row < bs && kq * kKW + kk < cs) ? (double)__ldg(rp + (int64_t)kk * n) : 0.0;
+        }
         if (tid == 0) wait_flag_b(&flags[(int64_t)c * ngroups + grp], want, spin, err);
-        __syncthreads();
-        if (row < bs) {
-            const TR* rp = R + (r0 + row) + cc0 * n;
-            const double* zp = Z + cc0 * W + c0g + 2 * cp;
-            for (int k = 0; k < cs; ++k) {
-                const double r = (double)__ldg(rp + (int64_t)k * n);
-                const double2 zz = __ldcg(reinterpret_cast<const double2*>(zp + (int64_t)k * W));
-                acc0 += r * zz.x;
-                acc1 += r * zz.y;
+        __syncthreads();   // the block is published, and every thread is done with the previous zs
+        if (zk < kTB) {
+            double2 a = make_double2(0.0, 0.0), e = make_double2(0.0, 0.0);
+            if (zk < cs) {
+                const double2* zp = reinterpret_cast<const double2*>(Z + (cc0 + zk) * W + c0g + zj);
+                a = __ldcg(zp);
+                e = __ldcg(zp + 1);
             }
+            zs[zk][zj] = a.x;
+            zs[zk][zj + 1] = a.y;
+            zs[zk][zj + 2] = e.x;
+            zs[zk][zj + 3] = e.y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kKW; ++kk) {
+            const double* zr = zs[kq * kKW + kk];
+#pragma unroll
+            for (int j = 0; j < kNR; ++j) acc[j] = fma(r[kk], zr[j], acc[j]);
         }
     }
-    __syncthreads();
-    if (row < bs) {
-        rhs[row][2 * cp] = V[(r0 + row) * W + c0g + 2 * cp] * cf[2 * cp][0] - acc0;
-        rhs[row][2 * cp + 1] = V[(r0 + row) * W + c0g + 2 * cp + 1] * cf[2 * cp + 1][0] - acc1;
-    } else {
-        rhs[row][2 * cp] = 0.0;
-        rhs[row][2 * cp + 1] = 0.0;
-    }
-    __syncthreads();
+    // the diagonal inverse's entries of this thread, before the right-hand side is complete
     const double* D = Dinv + (int64_t)b * kTB * kTB;
-    double z0 = 0.0, z1 = 0.0;
-    for (int k = 0; k < kTB; ++k) {
-        const double d = D[row + k * kTB];
-        z0 += d * rhs[k][2 * cp];
-        z1 += d * rhs[k][2 * cp + 1];
+    double d[kKW];
+#pragma unroll
+    for (int kk = 0; kk < kKW; ++kk) d[kk] = D[row + (kq * kKW + kk) * kTB];
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) part[kq][row][j] = acc[j];
+    __syncthreads();
+    const int cp = kq;   // epilogue: thread (row, cp) owns columns 2 cp, 2 cp + 1
+    for (int h = 0; h < 2; ++h) {
+        const int lc = 2 * cp + h;
+        const double s = ((part[0][row][lc] + part[1][row][lc]) + part[2][row][lc]) + part[3][row][lc];
+        rhs[row][lc] = row < bs ? V[(r0 + row) * W + c0g + lc] * cf[lc][0] - s : 0.0;
     }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) acc[j] = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < kKW; ++kk) {
+        const double* rr = rhs[kq * kKW + kk];
+#pragma unroll
+        for (int j = 0; j < kNR; ++j) acc[j] = fma(d[kk], rr[j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) part[kq][row][j] = acc[j];
+    __syncthreads();
     if (row < bs) {
         const int64_t base = (r0 + row) * W + c0g + 2 * cp;
-        Z[base] = z0;
-        Z[base + 1] = z1;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int lc = 2 * cp + h;
+            const double zv = ((part[0][row][lc] + part[1][row][lc]) + part[2][row][lc]) + part[3][row][lc];
+            Z[base + h] = zv;
             const double first = cf[lc][3];
             if (first < 0.0) continue;   // converged column: x and w stay as they are
-            const double zk = h == 0 ? z0 : z1;
             if (first != 0.0) {
-                WX[base + h] = zk;
+                WX[base + h] = zv;
             } else {
                 const double w = WX[base + h];
                 X[base + h] += cf[lc][1] * w;
-                WX[base + h] = zk - cf[lc][2] * w;
+                WX[base + h] = zv - cf[lc][2] * w;
             }
         }
     }
@@ -257,6 +293,9 @@ k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
 
 // MODE 2 (start): V = R^{-T} G, alpha_1. MODE 1: V = R^{-T} G - (beta/alpha) V, alpha, scalar steps.
 // The solve runs in place in G. CTA = (ticket k) -> block b = k / ngroups, group g = k % ngroups.
+// Thread (colr, kq) owns column r0 + colr of R (row colr of the block of R^T) and the quarter kq of
+// each 64-row block it multiplies: 16 contiguous entries, read before the wait for that block's
+// solution, as in the upper solve.
 template <class TR, int MODE>
 __global__ void __launch_bounds__(kBT)
 k_blk_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const double* __restrict__ Dinv, int W,
@@ -264,7 +303,9 @@ k_blk_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
                  long long spin, int* err) {
     __shared__ int tk_s;
     __shared__ unsigned epoch_s;
-    __shared__ double rhs[kTB][kNR];
+    __shared__ double zs[kTB][kNR];
+    __shared__ double part[kKQ][kTB][kNR + 1];
+    __shared__ double rhs[kTB][kNR + 1];
     __shared__ double coef[kNR];
     __shared__ double red[4][kNR];
     const int tid = threadIdx.x;
@@ -282,42 +323,88 @@ k_blk_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
     const int want = (int)(epoch_s + 1u);
     const int64_t r0 = (int64_t)b * kTB;
     const int bs = (int)(n - r0 < kTB ? n - r0 : kTB);
-    const int colr = tid & (kTB - 1), cp = tid >> 6;
-    double acc0 = 0.0, acc1 = 0.0;
-    for (int c = 0; c < b; ++c) {
+    const int colr = tid & (kTB - 1), kq = tid >> 6;
+    const int zk = tid >> 1, zj = (tid & 1) * 4;          // staging: threads 0..127, 4 values each
+    double acc[kNR];
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) acc[j] = 0.0;
+    for (int c = 0; c < b; ++c) {   // every block before b is a full 64-row block
         const int64_t cc0 = (int64_t)c * kTB;
-        if (tid == 0) wait_flag_b(&flags[(int64_t)c * ngroups + grp], want, spin, err);
-        __syncthreads();
-        if (colr < bs) {
-            const TR* rp = R + cc0 + (r0 + colr) * n;   // column r0 + colr, rows cc0 .. cc0 + 63
-            const double* gp = G + cc0 * W + c0g + 2 * cp;
-            for (int k = 0; k < kTB; ++k) {
-                const double r = (double)__ldg(rp + k);
-                const double2 gg = __ldcg(reinterpret_cast<const double2*>(gp + (int64_t)k * W));
-                acc0 += r * gg.x;
-                acc1 += r * gg.y;
+        double r[kKW];
+        {
+            const TR* rp = R + (cc0 + kq * kKW) + (r0 + colr) * n;   // column r0 + colr, 16 rows
+            if (colr < bs) {
+                if (sizeof(TR) == 8 && (reinterpret_cast<uintptr_t>(rp) & 15) == 0) {
+                    const double2* rp2 = reinterpret_cast<const double2*>(rp);
+#pragma unroll
+                    for (int kk = 0; kk < kKW; kk += 2) {
+                        const double2 t = __ldg(rp2 + kk / 2);
+                        r[kk] = t.x;
+                        r[kk + 1] = t.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < kKW; ++kk) r[kk] = (double)__ldg(rp + kk);
+                }
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < kKW; ++kk) r[kk] = 0.0;
             }
         }
+        if (tid == 0) wait_flag_b(&flags[(int64_t)c * ngroups + grp], want, spin, err);
+        __syncthreads();   // the block is published, and every thread is done with the previous zs
+        if (zk < kTB) {
+            const double2* gp = reinterpret_cast<const double2*>(G + (cc0 + zk) * W + c0g + zj);
+            const double2 a = __ldcg(gp), e = __ldcg(gp + 1);
+            zs[zk][zj] = a.x;
+            zs[zk][zj + 1] = a.y;
+            zs[zk][zj + 2] = e.x;
+            zs[zk][zj + 3] = e.y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kKW; ++kk) {
+            const double* zr = zs[kq * kKW + kk];
+#pragma unroll
+            for (int j = 0; j < kNR; ++j) acc[j] = fma(r[kk], zr[j], acc[j]);
+        }
+    }
+    // D^T: this thread's 16 contiguous entries of column colr of the diagonal inverse
+    const double2* D2 = reinterpret_cast<const double2*>(Dinv + (int64_t)b * kTB * kTB + colr * kTB + kq * kKW);
+    double d[kKW];
+#pragma unroll
+    for (int kk = 0; kk < kKW; kk += 2) {
+        const double2 t = D2[kk / 2];
+        d[kk] = t.x;
+        d[kk + 1] = t.y;
+    }
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) part[kq][colr][j] = acc[j];
+    __syncthreads();
+    const int cp = kq;   // thread (colr, cp) owns columns 2 cp, 2 cp + 1 from here on
+    for (int h = 0; h < 2; ++h) {
+        const int lc = 2 * cp + h;
+        const double s = ((part[0][colr][lc] + part[1][colr][lc]) + part[2][colr][lc]) + part[3][colr][lc];
+        rhs[colr][lc] = colr < bs ? G[(r0 + colr) * W + c0g + lc] - s : 0.0;
     }
     __syncthreads();
-    if (colr < bs) {
-        rhs[colr][2 * cp] = G[(r0 + colr) * W + c0g + 2 * cp] - acc0;
-        rhs[colr][2 * cp + 1] = G[(r0 + colr) * W + c0g + 2 * cp + 1] - acc1;
-    } else {
-        rhs[colr][2 * cp] = 0.0;
-        rhs[colr][2 * cp + 1] = 0.0;
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) acc[j] = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < kKW; ++kk) {
+        const double* rr = rhs[kq * kKW + kk];
+#pragma unroll
+        for (int j = 0; j < kNR; ++j) acc[j] = fma(d[kk], rr[j], acc[j]);
     }
+#pragma unroll
+    for (int j = 0; j < kNR; ++j) part[kq][colr][j] = acc[j];
     __syncthreads();
-    const double* D = Dinv + (int64_t)b * kTB * kTB;
-    double z0 = 0.0, z1 = 0.0;
-    for (int k = 0; k < kTB; ++k) {
-        const double d = D[k + colr * kTB];
-        z0 += d * rhs[k][2 * cp];
-        z1 += d * rhs[k][2 * cp + 1];
-    }
     double sq0 = 0.0, sq1 = 0.0;
     if (colr < bs) {
         const int64_t base = (r0 + colr) * W + c0g + 2 * cp;
+        const double z0 = ((part[0][colr][2 * cp] + part[1][colr][2 * cp]) + part[2][colr][2 * cp]) + part[3][colr][2 * cp];
+        const double z1 = ((part[0][colr][2 * cp + 1] + part[1][colr][2 * cp + 1]) + part[2][colr][2 * cp + 1]) +
+                          part[3][colr][2 * cp + 1];
         G[base] = z0;
         G[base + 1] = z1;
         const double v0 = MODE == 1 ? z0 - coef[2 * cp] * V[base] : z0;

@@ -167,6 +167,7 @@ def config_problem(name):
     cfg5_slice 1,000 x 100 with the cfg5 recipe
     rfm6x6     2D Poisson, 6x6 boxes, J=200, 30x30 points, R=2, seed 2     36,720 x 7,200 (profiling size:
                its 28,800 x 7,200 sketch is 1.7 GB, above L2 and well below HBM)
+    rfm6x6_64  rfm6x6's matrix with cfg4a's 64 right-hand sides (profiling size of the block solve)
     c1_<name>  rank-deficient stand-in with the shape, rank and density of Table C.1's <name>
     """
     if name == "cfg1":
@@ -182,6 +183,9 @@ def config_problem(name):
         return scaled_random_sparse(2_000_000, 20_000, seed=5)
     if name == "rfm6x6":
         return poisson2d(6, 6, 200, 30, 30, R=2.0, seed=2)
+    if name == "rfm6x6_64":
+        modes = [(a, b) for a in range(1, 9) for b in range(1, 9)]
+        return poisson2d(6, 6, 200, 30, 30, R=2.0, seed=2, modes=modes)
     if name == "cfg5_slice":
         return scaled_random_sparse(1000, 100, seed=5)
     if name.startswith("c1_") and name[3:] in TABLE_C1_SHAPES:
