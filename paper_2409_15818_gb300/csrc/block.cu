@@ -172,9 +172,9 @@ k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
                  long long spin, int* err) {
     __shared__ int tk_s;
     __shared__ unsigned epoch_s;
-    __shared__ double zs[kTB][kNR];             // the solution block being multiplied (group columns)
+    __shared__ __align__(16) double zs[kTB][kNR];   // the solution block being multiplied (group columns)
     __shared__ double part[kKQ][kTB][kNR + 1];  // per-quarter partial sums (padded rows: no bank conflicts)
-    __shared__ double rhs[kTB][kNR + 1];
+    __shared__ __align__(16) double rhs[kTB][kNR];
     __shared__ double cf[kNR][4];   // 1/alpha, cx, cw, first (0 for converged columns)
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -219,17 +219,19 @@ k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
                 a = __ldcg(zp);
                 e = __ldcg(zp + 1);
             }
-            zs[zk][zj] = a.x;
-            zs[zk][zj + 1] = a.y;
-            zs[zk][zj + 2] = e.x;
-            zs[zk][zj + 3] = e.y;
+            reinterpret_cast<double2*>(&zs[zk][zj])[0] = a;
+            reinterpret_cast<double2*>(&zs[zk][zj])[1] = e;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kKW; ++kk) {
-            const double* zr = zs[kq * kKW + kk];
+            const double2* zr = reinterpret_cast<const double2*>(zs[kq * kKW + kk]);
 #pragma unroll
-            for (int j = 0; j < kNR; ++j) acc[j] = fma(r[kk], zr[j], acc[j]);
+            for (int j = 0; j < kNR / 2; ++j) {
+                const double2 t = zr[j];
+                acc[2 * j] = fma(r[kk], t.x, acc[2 * j]);
+                acc[2 * j + 1] = fma(r[kk], t.y, acc[2 * j + 1]);
+            }
         }
     }
     // the diagonal inverse's entries of this thread, before the right-hand side is complete
@@ -251,9 +253,13 @@ k_blk_trsv_upper(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
     for (int j = 0; j < kNR; ++j) acc[j] = 0.0;
 #pragma unroll
     for (int kk = 0; kk < kKW; ++kk) {
-        const double* rr = rhs[kq * kKW + kk];
+        const double2* rr = reinterpret_cast<const double2*>(rhs[kq * kKW + kk]);
 #pragma unroll
-        for (int j = 0; j < kNR; ++j) acc[j] = fma(d[kk], rr[j], acc[j]);
+        for (int j = 0; j < kNR / 2; ++j) {
+            const double2 t = rr[j];
+            acc[2 * j] = fma(d[kk], t.x, acc[2 * j]);
+            acc[2 * j + 1] = fma(d[kk], t.y, acc[2 * j + 1]);
+        }
     }
 #pragma unroll
     for (int j = 0; j < kNR; ++j) part[kq][row][j] = acc[j];
@@ -303,9 +309,9 @@ k_blk_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
                  long long spin, int* err) {
     __shared__ int tk_s;
     __shared__ unsigned epoch_s;
-    __shared__ double zs[kTB][kNR];
+    __shared__ __align__(16) double zs[kTB][kNR];
     __shared__ double part[kKQ][kTB][kNR + 1];
-    __shared__ double rhs[kTB][kNR + 1];
+    __shared__ __align__(16) double rhs[kTB][kNR];
     __shared__ double coef[kNR];
     __shared__ double red[4][kNR];
     const int tid = threadIdx.x;
@@ -356,17 +362,19 @@ k_blk_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
         if (zk < kTB) {
             const double2* gp = reinterpret_cast<const double2*>(G + (cc0 + zk) * W + c0g + zj);
             const double2 a = __ldcg(gp), e = __ldcg(gp + 1);
-            zs[zk][zj] = a.x;
-            zs[zk][zj + 1] = a.y;
-            zs[zk][zj + 2] = e.x;
-            zs[zk][zj + 3] = e.y;
+            reinterpret_cast<double2*>(&zs[zk][zj])[0] = a;
+            reinterpret_cast<double2*>(&zs[zk][zj])[1] = e;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kKW; ++kk) {
-            const double* zr = zs[kq * kKW + kk];
+            const double2* zr = reinterpret_cast<const double2*>(zs[kq * kKW + kk]);
 #pragma unroll
-            for (int j = 0; j < kNR; ++j) acc[j] = fma(r[kk], zr[j], acc[j]);
+            for (int j = 0; j < kNR / 2; ++j) {
+                const double2 t = zr[j];
+                acc[2 * j] = fma(r[kk], t.x, acc[2 * j]);
+                acc[2 * j + 1] = fma(r[kk], t.y, acc[2 * j + 1]);
+            }
         }
     }
     // D^T: this thread's 16 contiguous entries of column colr of the diagonal inverse
@@ -392,9 +400,13 @@ k_blk_trsv_lower(const TR* __restrict__ R, int64_t n, int nb, int ngroups, const
     for (int j = 0; j < kNR; ++j) acc[j] = 0.0;
 #pragma unroll
     for (int kk = 0; kk < kKW; ++kk) {
-        const double* rr = rhs[kq * kKW + kk];
+        const double2* rr = reinterpret_cast<const double2*>(rhs[kq * kKW + kk]);
 #pragma unroll
-        for (int j = 0; j < kNR; ++j) acc[j] = fma(d[kk], rr[j], acc[j]);
+        for (int j = 0; j < kNR / 2; ++j) {
+            const double2 t = rr[j];
+            acc[2 * j] = fma(d[kk], t.x, acc[2 * j]);
+            acc[2 * j + 1] = fma(d[kk], t.y, acc[2 * j + 1]);
+        }
     }
 #pragma unroll
     for (int j = 0; j < kNR; ++j) part[kq][colr][j] = acc[j];
