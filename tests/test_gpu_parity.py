@@ -277,6 +277,33 @@ def test_multi_rhs_fixed_iterations_track_single(csls):
         assert _rel(X[k].cpu().numpy(), xo) < 1e-10
 
 
+def test_multi_rhs_block_pieces_track_oracle(csls):
+    """n = 4,800: R has 75 diagonal blocks, so the block triangular solves hand each step's products with
+    solutions more than 32 steps old to worker CTAs (up to three pieces a step, summed in piece order).
+    Twelve right-hand sides (a half-empty second group of 8): after 8 fixed iterations each column matches
+    the oracle's LSQR run with the same R to 1e-10, and the tol-plus-restart solutions match the single
+    right-hand-side solves in the A-norm to 1e-10."""
+    rng = np.random.default_rng(31)
+    A = random_sparse(20000, 4800, 10, rng, scale_exp=3.0)
+    assert (A.n + 63) // 64 > 2 * 32 + 1
+    Bn = rng.standard_normal((12, 20000))
+    Ag = dev(csls, A)
+    F = csls.csls_factor(Ag, seed=5)
+    R = F.R().cpu().numpy()
+    B = torch.tensor(Bn, device="cuda")
+    X, rep = csls.csls_solve(F, Ag, B, fixed_iters=8)
+    assert rep["iterations"] == 8
+    for k in (0, 7, 8, 11):
+        xo, _ = oracle.lsqr(A, Bn[k], R, "qr", fixed_iters=8)
+        assert _rel(X[k].cpu().numpy(), xo) < 1e-10
+    X2, rep2 = csls.csls_solve(F, Ag, B, tol=1e-8, refine=1)
+    assert rep2["status"] == 0
+    for k in (0, 9):
+        xk, _ = csls.csls_solve(F, Ag, B[k], tol=1e-8, refine=1)
+        xb, xs = X2[k].cpu().numpy(), xk.cpu().numpy()
+        assert np.linalg.norm(oracle.spmv(A, xb - xs)) <= 1e-10 * np.linalg.norm(oracle.spmv(A, xs))
+
+
 def test_svd_variant_rank_deficient(csls):
     rng = np.random.default_rng(24)
     base = random_sparse(900, 40, 6, rng).dense()
