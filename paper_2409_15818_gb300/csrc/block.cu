@@ -6,7 +6,7 @@
 // products. The triangular solves are chains of per-block steps (tickets, per-block
 // flags with bounded waits) with 8 right-hand sides per CTA, so the chains of the
 // column groups run side by side; the products of a step with older solutions are
-// split off to worker CTAs in pieces of 32 steps (see blk_products).
+// split off to worker CTAs in pieces of at least 32 steps (see blk_products).
 #include <algorithm>
 #include <cstring>
 #include <vector>
